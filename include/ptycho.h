@@ -1,0 +1,168 @@
+/*
+ * ptycho.h — C ABI of the GB300 blind-ptychography set-projection library.
+ *
+ * Method: W. Mei, A. M. Maiden, "Set projection algorithms for blind
+ * ptychographic phase retrieval" (arXiv 2311.11466).  One call of
+ * ptycho_iterate runs the paper's generalised divide-and-concur update
+ * (Introduction, the displayed equation)
+ *
+ *     x_{k+1} = a P^b_C P^c_D x_k + (1 - a) x_k
+ *
+ * over the stack x = [x_0 .. x_{J-1}] of per-position exit waves (the product
+ * space of Fig. 3), following the flow of Fig. 4: exit waves for all scan
+ * positions -> projections -> updated probe and object.
+ *
+ *   P_D  (divide, Fig. 3(a)): per position, Psi = F x_j, replace |Psi| by the
+ *        measured sqrt(I_j) (phase kept; sqrt(I_j) where Psi = 0), F^{-1}.
+ *   P_C  (concur, Fig. 3(b)): least-squares consensus {P * O_j}: the object
+ *        from the current probe, then the probe from the new object, each as
+ *        sum conj(.) y / (sum |.|^2 + alpha * max(sum |.|^2)), re-split z_j = P * O_j.
+ *   P^a_S = a P^1_S + (1 - a) I (relaxed projection, Introduction).
+ *
+ * DC = (1,1,1), AR = (1,2,2), DR = (1/2,2,2), SF = (1,2,1),
+ * RAAR(beta) = (1/2, 2 beta, 2), RRR(beta) = (beta/2, 2, 2) are settings of the
+ * same call.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - F is the unnormalised 2-D DFT exp(-2 pi i q.r / N); F^{-1} carries 1/N^2;
+ *    no fftshift: intensities are stored with zero frequency at [0][0].
+ *  - Complex arrays are interleaved float32 (re, im), row-major:
+ *    object [M_rows][M_cols][2], probe [N][N][2], exit waves [J][N][N][2].
+ *  - Positions are int32 [J][2] = (row, col) of the window's top-left corner
+ *    in the object: O_j(r) = O(s_j + r), r in [0, N)^2.
+ *  - Every function returns a ptycho_status; on error, ptycho_last_error()
+ *    gives a one-line reason.  Inputs are copied: the caller keeps ownership
+ *    of every buffer it passes.  Outputs go to caller-allocated host buffers.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - All device work of a context runs on its stream, asynchronously unless a
+ *    function says it synchronises.
+ */
+#ifndef PTYCHO_H
+#define PTYCHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PTYCHO_OK = 0,
+    PTYCHO_EINVAL = -1,    /* bad argument (size, range, non-finite value) */
+    PTYCHO_ENOMEM = -2,    /* device allocation failed or exceeds a budget */
+    PTYCHO_ECUDA = -3,     /* a CUDA runtime call failed */
+    PTYCHO_ETIMEOUT = -4,  /* a bounded device wait expired */
+    PTYCHO_ESTATE = -5     /* call not valid in the context's current state */
+} ptycho_status;
+
+/* Precision of the divide step's transforms. */
+enum { PTYCHO_PREC_FP32 = 0,    /* FP32 shared-memory FFT (default) */
+       PTYCHO_PREC_BF16X3 = 1   /* DFT as dense GEMMs on tensor cores, BF16 hi/lo
+                                   split with three products, FP32 accumulation */ };
+
+/* How the concur step accumulates the object. */
+enum { PTYCHO_CONCUR_DETERMINISTIC = 0,  /* position-tiled gather, fixed order */
+       PTYCHO_CONCUR_ATOMIC = 1 };       /* per-position scatter with atomics */
+
+typedef struct {
+    int device;      /* CUDA device ordinal */
+    int precision;   /* PTYCHO_PREC_* */
+    int concur;      /* PTYCHO_CONCUR_* */
+    float alpha;     /* denominator regulariser, >= 0 (default 1e-6) */
+    void* stream;    /* cudaStream_t to run on, or NULL for a private stream */
+} ptycho_opts;
+
+typedef struct ptycho_ctx ptycho_ctx;
+
+/* Fill *opts with the defaults (device 0, FP32, deterministic, alpha 1e-6). */
+void ptycho_default_opts(ptycho_opts* opts);
+
+/* Create a context on opts->device.  opts may be NULL for the defaults.
+ * Errors: EINVAL (bad option), ECUDA. */
+int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts);
+
+/* Release every device allocation of the context.  NULL is a no-op. */
+void ptycho_destroy(ptycho_ctx* ctx);
+
+/* Last error message of the context ("" if none); never NULL.  With
+ * ctx == NULL, the last error of ptycho_create on this thread. */
+const char* ptycho_last_error(const ptycho_ctx* ctx);
+
+/* Flags of ptycho_load_scan. */
+enum { PTYCHO_LOAD_INTENSITY_DEVICE = 1u };  /* intensity is a device pointer */
+
+/* Load one scan and form the initial exit waves x_0,j = P_0 * O_0(s_j + .)
+ * (Fig. 4, the first box).  Replaces any scan already loaded.
+ *   J          number of positions, >= 1
+ *   N          pattern side: 8, 16, 32, 64, 128 or 256
+ *   pos_rc     host int32 [J][2]; each must satisfy 0 <= row <= M_rows - N and
+ *              0 <= col <= M_cols - N (never clamped: out of range is EINVAL)
+ *   intensity  float32 [J][N][N] measured intensities, unshifted, finite, >= 0;
+ *              host memory unless flags has PTYCHO_LOAD_INTENSITY_DEVICE
+ *   M_rows, M_cols  object size, each >= N
+ *   obj0       host complex float32 [M_rows][M_cols], finite (initial object)
+ *   probe0     host complex float32 [N][N], finite (initial probe)
+ * Synchronises the context's stream.  Errors: EINVAL, ENOMEM, ECUDA. */
+int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_rc,
+                     const float* intensity, int32_t M_rows, int32_t M_cols,
+                     const float* obj0, const float* probe0, uint32_t flags);
+
+/* Run n_iter iterations of x <- a P^b_C P^c_D x + (1 - a) x, appending the
+ * Fourier error E_F(x_k) = sum (|F x_k| - sqrt(I))^2 / sum I of each
+ * iteration's input to the context's error history.  Asynchronous on the
+ * context's stream.  n_iter = 0 is a no-op.
+ * Errors: EINVAL (a, b, c not finite, n_iter < 0), ESTATE (no scan), ECUDA. */
+int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter);
+
+/* Copy the current object [M_rows][M_cols][2] and probe [N][N][2] to host
+ * buffers (either may be NULL).  Synchronises.  Errors: ESTATE, ECUDA. */
+int ptycho_get_object_probe(ptycho_ctx* ctx, float* obj_out, float* probe_out);
+
+/* Overwrite the object and/or probe (host buffers, either may be NULL).
+ * The exit waves are not changed.  Errors: EINVAL (non-finite), ESTATE, ECUDA. */
+int ptycho_set_object_probe(ptycho_ctx* ctx, const float* obj, const float* probe);
+
+/* Copy the current iterate x_k [J][N][N][2] to a host buffer.  Synchronises.
+ * Errors: ESTATE, ECUDA. */
+int ptycho_get_exit_waves(ptycho_ctx* ctx, float* x_out);
+
+/* Replace the current iterate x_k by a host buffer [J][N][N][2].
+ * Errors: EINVAL (non-finite), ESTATE, ECUDA. */
+int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* x);
+
+/* Copy up to cap entries of the per-iteration Fourier-error history (oldest
+ * first, since the last load) to fourier_err; *n_written receives the count.
+ * The history keeps the most recent 65536 iterations.  Synchronises.
+ * Errors: EINVAL (cap < 0 or NULL pointers with cap > 0), ESTATE, ECUDA. */
+int ptycho_errors(ptycho_ctx* ctx, double* fourier_err, int32_t cap, int32_t* n_written);
+
+/* Number of iterations run since the last load (0 without a scan). */
+int64_t ptycho_iteration_count(const ptycho_ctx* ctx);
+
+/* Fourier error of the consensus model, E_F(z) with z_j = P * O(s_j + .),
+ * for the current object and probe (the final error of a reconstruction).
+ * Synchronises.  Errors: ESTATE, ECUDA. */
+int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err);
+
+/* Kernel timing for measurement: with enable = 1 the context records CUDA
+ * events on its stream around every later launch of the divide kernel and of
+ * the concur step (up to 4096 iterations); enable = 0 stops recording, and a
+ * new enable = 1 clears what was recorded.  Errors: EINVAL, ECUDA. */
+int ptycho_profile_enable(ptycho_ctx* ctx, int enable);
+
+/* Sum of the recorded divide-kernel and concur-step durations in ms and the
+ * number of iterations recorded.  Synchronises.  Errors: EINVAL, ECUDA. */
+int ptycho_profile_read(ptycho_ctx* ctx, double* divide_ms, double* concur_ms, int32_t* n_iters);
+
+/* Bytes of device memory the context holds for its current scan. */
+size_t ptycho_device_bytes(const ptycho_ctx* ctx);
+
+/* Bytes of device memory a scan of this size would need (for admission). */
+size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, int precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYCHO_H */

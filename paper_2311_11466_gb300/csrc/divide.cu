@@ -1,0 +1,446 @@
+// Divide step P^c_D of the abc update (Introduction; Fig. 3(a)), fused with
+// the relaxed re-split of the previous iteration's concur step:
+//
+//   x_k  = a' (b' P O_j + (1 - b') y_{k-1}) + (1 - a') x_{k-1}     (or x_k given)
+//   Psi  = F x_k
+//   y_k  = F^{-1}( c sqrt(I_j) Psi/|Psi| + (1 - c) Psi )
+//   e_j  = sum_q (|Psi| - sqrt(I_j))^2
+//
+// One thread-block cluster of C CTAs owns one N x N exit wave; CTA c holds
+// R = N / C consecutive rows in shared memory (FP32 complex).  The 2-D DFT is
+// a row DFT, a cluster-wide transpose through distributed shared memory, and
+// a second row DFT; every 1-D DFT of length N = A * B runs as two in-register
+// radix passes (length A over stride-B elements, a twiddle, length B across
+// threads) in place in shared memory.  The spectrum therefore sits in a
+// digit-permuted order; sqrt(I) is stored in that same order at load time so
+// the modulus step reads it with contiguous vector loads.
+//
+// Shared-memory row layout: the element of 1-D index t + B e (t < B, e < A)
+// lives at slot e (B + 1) + t, so stage-1 threads (fixed e across lanes) and
+// stage-2 threads (contiguous runs of B) are both bank-conflict free; the row
+// stride RS is congruent to 9 mod 16 complex so column-wise transposes are
+// conflict free as well.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ptycho {
+namespace {
+
+template <int N> struct Cfg;
+template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 64; };
+template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64; };
+template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128; };
+template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256; };
+template <> struct Cfg<128> { static constexpr int A = 16, B = 8,  C = 4, T = 256; };
+template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 8, T = 256; };
+
+template <int N>
+struct Geo {
+    static constexpr int A = Cfg<N>::A, B = Cfg<N>::B, C = Cfg<N>::C, T = Cfg<N>::T;
+    static constexpr int R = N / C;       // rows per CTA
+    static constexpr int KC = A / C;      // stage-2 indices (k1) owned per CTA after the transpose
+    static constexpr int RS0 = A * (B + 1);
+    static constexpr int RS = RS0 + ((9 - RS0 % 16) + 16) % 16;  // row stride, = 9 mod 16
+    static constexpr int PER = R * R / T;  // transpose elements per thread per partner block
+    static constexpr int GT = C < 4 ? C : 4;  // partner blocks exchanged per cluster barrier
+    static constexpr size_t SMEM = (size_t)R * RS * sizeof(float2) + N * sizeof(float2) +
+                                   32 * sizeof(double);
+    static_assert(A * B == N, "radix split");
+    static_assert(A % C == 0, "cluster split");
+    static_assert((R * R) % T == 0, "transpose split");
+    static_assert(C % GT == 0, "exchange rounds");
+};
+
+// Slot of the spectral index with stage-2 index k (= k1) and stage-2 output k2.
+template <int N>
+__device__ __forceinline__ int slot_freq(int cta, int q) {
+    using G = Geo<N>;
+    return (cta * G::KC + q / G::B) * (G::B + 1) + q % G::B;
+}
+// Slot of spatial index r = t + B e.
+template <int N>
+__device__ __forceinline__ int slot_space(int r) {
+    using G = Geo<N>;
+    return (r / G::B) * (G::B + 1) + r % G::B;
+}
+
+// Cluster-wide transpose.  FWD: rows (spatial) x spectral slots  ->  this
+// CTA's spectral indices x all spatial rows.  !FWD: the reverse.  Partner
+// blocks are exchanged in rounds (partner = rank XOR d): read the partner's
+// block into registers, cluster barrier, overwrite the same block locally;
+// the partner reads exactly the block this CTA overwrites in the same round.
+template <int N, bool FWD>
+__device__ __forceinline__ void exchange(float2* buf, cg::cluster_group& cl, int c) {
+    using G = Geo<N>;
+    constexpr int R = G::R, RS = G::RS, T = G::T, PER = G::PER, GT = G::GT, C = G::C;
+#pragma unroll 1
+    for (int g = 0; g < C; g += GT) {
+        float2 reg[GT][PER];
+#pragma unroll
+        for (int d = 0; d < GT; ++d) {
+            const int p = c ^ (g + d);
+            const float2* src = cl.map_shared_rank(buf, p);
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int e = threadIdx.x + T * m;
+                if (FWD) {
+                    const int q = e % R, i = e / R;
+                    reg[d][m] = src[i * RS + slot_freq<N>(c, q)];
+                } else {
+                    const int i = e % R, q = e / R;
+                    reg[d][m] = src[q * RS + slot_space<N>(R * c + i)];
+                }
+            }
+        }
+        cl.sync();
+#pragma unroll
+        for (int d = 0; d < GT; ++d) {
+            const int p = c ^ (g + d);
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int e = threadIdx.x + T * m;
+                if (FWD) {
+                    const int q = e % R, i = e / R;
+                    buf[q * RS + slot_space<N>(R * p + i)] = reg[d][m];
+                } else {
+                    const int i = e % R, q = e / R;
+                    buf[i * RS + slot_freq<N>(p, q)] = reg[d][m];
+                }
+            }
+        }
+    }
+}
+
+template <int N, bool ERR_ONLY>
+__global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args) {
+    using G = Geo<N>;
+    constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = buf + R * RS;
+    double* red = reinterpret_cast<double*>(tw + N);
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const int j = blockIdx.x / C;
+    const int tid = threadIdx.x;
+
+    for (int i = tid; i < N; i += T) tw[i] = args.tw[i];
+    __syncthreads();
+
+    const int2 s = args.pos[j];
+    const size_t pat = (size_t)j * N * N;
+    const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
+    const bool load_x = args.load_x != 0, write_x = args.write_x != 0;
+    const bool need_y = args.pb != 1.0f, need_xp = args.pa != 1.0f;
+
+    // Phase 1: form x_k and run the row DFT's first pass.
+#pragma unroll 1
+    for (int task = tid; task < R * B; task += T) {
+        const int row = task / B, t = task % B;
+        const int r = c * R + row;
+        float2 v[A];
+#pragma unroll
+        for (int e = 0; e < A; ++e) {
+            const int n = t + B * e;
+            const size_t idx = pat + (size_t)r * N + n;
+            float2 xv;
+            if (load_x) {
+                xv = args.x[idx];
+            } else {
+                const float2 z = cmul_rn(args.P[r * N + n], Ow[(size_t)r * args.Mc + n]);
+                const float2 yv = need_y ? args.y[idx] : make_float2(0.f, 0.f);
+                const float2 xp = need_xp ? args.x[idx] : make_float2(0.f, 0.f);
+                xv = resplit_rn(z, yv, xp, args.pa, args.pb);
+                if (write_x) args.x[idx] = xv;
+            }
+            v[e] = xv;
+        }
+        dft_reg<A, false>(v);
+#pragma unroll
+        for (int k = 0; k < A; ++k) buf[row * RS + k * (B + 1) + t] = cmul(v[k], tw[k * B + t]);
+    }
+    __syncthreads();
+
+    // Phase 2: row DFT second pass (frequency k1 + A k2 -> slot (k2, k1)).
+#pragma unroll 1
+    for (int task = tid; task < R * A; task += T) {
+        const int row = task / A, k = task % A;
+        float2* p = buf + row * RS + k * (B + 1);
+        float2 u[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) u[t] = p[t];
+        dft_reg<B, false>(u);
+#pragma unroll
+        for (int t = 0; t < B; ++t) p[t] = u[t];
+    }
+    cl.sync();
+    exchange<N, true>(buf, cl, c);
+    __syncthreads();
+
+    // Phase 3: column DFT first pass (rows now hold whole columns).
+#pragma unroll 1
+    for (int task = tid; task < R * B; task += T) {
+        const int row = task / B, t = task % B;
+        float2* p = buf + row * RS + t;
+        float2 v[A];
+#pragma unroll
+        for (int e = 0; e < A; ++e) v[e] = p[e * (B + 1)];
+        dft_reg<A, false>(v);
+#pragma unroll
+        for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], tw[k * B + t]);
+    }
+    __syncthreads();
+
+    // Phase 4: column DFT second pass, Fourier-modulus projection with the
+    // c relaxation and the 1/N^2 of the inverse, inverse second pass.
+    float err = 0.f;
+    const float* sq = args.sqrtIp + pat + (size_t)c * R * N;
+    const float inv_n2 = 1.0f / (float)(N * N);
+    const float cr = args.c, oc = 1.0f - args.c;
+#pragma unroll 1
+    for (int task = tid; task < R * A; task += T) {
+        const int row = task / A, k = task % A;
+        float2* p = buf + row * RS + k * (B + 1);
+        float2 u[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) u[t] = p[t];
+        dft_reg<B, false>(u);
+        float sv[B];
+        const float* sp = sq + (size_t)(row * A + k) * B;
+        if constexpr (B % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < B; q += 4) {
+                const float4 f = *reinterpret_cast<const float4*>(sp + q);
+                sv[q] = f.x; sv[q + 1] = f.y; sv[q + 2] = f.z; sv[q + 3] = f.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < B; ++q) sv[q] = sp[q];
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const float m2 = cabs2(u[q]);
+            const float mag = sqrtf(m2);
+            const float d = mag - sv[q];
+            err = fmaf(d, d, err);
+            if constexpr (!ERR_ONLY) {
+                float2 pr;
+                if (m2 > 0.f) {
+                    pr = cscale(u[q], sv[q] / mag);
+                } else {
+                    pr = make_float2(sv[q], 0.f);
+                }
+                u[q] = make_float2(fmaf(cr, pr.x, oc * u[q].x) * inv_n2,
+                                   fmaf(cr, pr.y, oc * u[q].y) * inv_n2);
+            }
+        }
+        if constexpr (!ERR_ONLY) {
+            dft_reg<B, true>(u);
+#pragma unroll
+            for (int t = 0; t < B; ++t) p[t] = cconjmul(tw[k * B + t], u[t]);
+        }
+    }
+
+    if constexpr (!ERR_ONLY) {
+        __syncthreads();
+        // Phase 5: column inverse first pass (natural spatial order).
+#pragma unroll 1
+        for (int task = tid; task < R * B; task += T) {
+            const int row = task / B, t = task % B;
+            float2* p = buf + row * RS + t;
+            float2 v[A];
+#pragma unroll
+            for (int k = 0; k < A; ++k) v[k] = p[k * (B + 1)];
+            dft_reg<A, true>(v);
+#pragma unroll
+            for (int e = 0; e < A; ++e) p[e * (B + 1)] = v[e];
+        }
+        cl.sync();
+        exchange<N, false>(buf, cl, c);
+        __syncthreads();
+
+        // Phase 6: row inverse second pass with the conjugate twiddle.
+#pragma unroll 1
+        for (int task = tid; task < R * A; task += T) {
+            const int row = task / A, k = task % A;
+            float2* p = buf + row * RS + k * (B + 1);
+            float2 u[B];
+#pragma unroll
+            for (int t = 0; t < B; ++t) u[t] = p[t];
+            dft_reg<B, true>(u);
+#pragma unroll
+            for (int t = 0; t < B; ++t) p[t] = cconjmul(tw[k * B + t], u[t]);
+        }
+        __syncthreads();
+
+        // Phase 7: row inverse first pass, store y_k.
+#pragma unroll 1
+        for (int task = tid; task < R * B; task += T) {
+            const int row = task / B, t = task % B;
+            const int r = c * R + row;
+            const float2* p = buf + row * RS + t;
+            float2 v[A];
+#pragma unroll
+            for (int k = 0; k < A; ++k) v[k] = p[k * (B + 1)];
+            dft_reg<A, true>(v);
+            float2* yo = args.y + pat + (size_t)r * N + t;
+#pragma unroll
+            for (int e = 0; e < A; ++e) yo[B * e] = v[e];
+        }
+    }
+
+    const double tot = block_sum_double<T>((double)err, red);
+    if (tid == 0) args.e_part[(size_t)j * C + c] = tot;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) sqrt_permute_kernel(const float* __restrict__ I,
+                                                           float* __restrict__ sqrtIp,
+                                                           double* __restrict__ psum,
+                                                           int* __restrict__ bad) {
+    using G = Geo<N>;
+    constexpr int A = G::A, B = G::B, R = G::R, KC = G::KC;
+    __shared__ double red[8];
+    const int j = blockIdx.y;
+    const int pidx = blockIdx.x * 256 + threadIdx.x;
+    double v64 = 0.0;
+    if (pidx < N * N) {
+        // pidx = ((cta * R + rho) * A + k1p) * B + k2p
+        const int k2p = pidx % B;
+        int tmp = pidx / B;
+        const int k1p = tmp % A;
+        tmp /= A;
+        const int rho = tmp % R;
+        const int cta = tmp / R;
+        const int u = k1p + A * k2p;                       // row frequency
+        const int v = (cta * KC + rho / B) + A * (rho % B);  // column frequency
+        const float val = I[(size_t)j * N * N + (size_t)u * N + v];
+        if (!(val >= 0.0f) || !isfinite(val)) atomicOr(bad, 1);
+        sqrtIp[(size_t)j * N * N + pidx] = sqrtf(fmaxf(val, 0.0f));
+        v64 = (double)val;
+    }
+    const double tot = block_sum_double<256>(v64, red);
+    if (threadIdx.x == 0) psum[(size_t)j * gridDim.x + blockIdx.x] = tot;
+}
+
+template <int N>
+cudaError_t prepare_t() {
+    cudaError_t e = cudaFuncSetAttribute(divide_kernel<N, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(divide_kernel<N, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<N>::SMEM);
+}
+
+template <int N>
+cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
+    using G = Geo<N>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.J * G::C);
+    cfg.blockDim = dim3(G::T);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (a.err_only) return cudaLaunchKernelEx(&cfg, divide_kernel<N, true>, a);
+    return cudaLaunchKernelEx(&cfg, divide_kernel<N, false>, a);
+}
+
+template <int N>
+cudaError_t sqrt_t(const float* I, float* sqrtIp, double* psum, int* bad, int J, cudaStream_t st) {
+    dim3 grid((N * N + 255) / 256, J);
+    sqrt_permute_kernel<N><<<grid, 256, 0, st>>>(I, sqrtIp, psum, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool divide_supported(int N) {
+    return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || N == 256;
+}
+
+int divide_cluster_size(int N) {
+    switch (N) {
+        case 8: return Geo<8>::C;
+        case 16: return Geo<16>::C;
+        case 32: return Geo<32>::C;
+        case 64: return Geo<64>::C;
+        case 128: return Geo<128>::C;
+        case 256: return Geo<256>::C;
+    }
+    return 0;
+}
+
+static void twiddles_ab(int N, int A, int B, std::vector<float2>& tw) {
+    tw.resize((size_t)N);
+    for (int k = 0; k < A; ++k)
+        for (int t = 0; t < B; ++t) {
+            const long m = ((long)t * k) % N;
+            const double ang = -2.0 * M_PI * (double)m / (double)N;
+            tw[(size_t)k * B + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+}
+
+void divide_twiddles(int N, std::vector<float2>& tw) {
+    switch (N) {
+        case 8: twiddles_ab(N, Geo<8>::A, Geo<8>::B, tw); break;
+        case 16: twiddles_ab(N, Geo<16>::A, Geo<16>::B, tw); break;
+        case 32: twiddles_ab(N, Geo<32>::A, Geo<32>::B, tw); break;
+        case 64: twiddles_ab(N, Geo<64>::A, Geo<64>::B, tw); break;
+        case 128: twiddles_ab(N, Geo<128>::A, Geo<128>::B, tw); break;
+        case 256: twiddles_ab(N, Geo<256>::A, Geo<256>::B, tw); break;
+        default: tw.clear();
+    }
+}
+
+cudaError_t divide_prepare(int N) {
+    switch (N) {
+        case 8: return prepare_t<8>();
+        case 16: return prepare_t<16>();
+        case 32: return prepare_t<32>();
+        case 64: return prepare_t<64>();
+        case 128: return prepare_t<128>();
+        case 256: return prepare_t<256>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st) {
+    switch (N) {
+        case 8: return launch_t<8>(a, st);
+        case 16: return launch_t<16>(a, st);
+        case 32: return launch_t<32>(a, st);
+        case 64: return launch_t<64>(a, st);
+        case 128: return launch_t<128>(a, st);
+        case 256: return launch_t<256>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sqrt_permute(int N, const float* I, float* sqrtIp, double* psum, int* bad,
+                                int J, cudaStream_t st) {
+    switch (N) {
+        case 8: return sqrt_t<8>(I, sqrtIp, psum, bad, J, st);
+        case 16: return sqrt_t<16>(I, sqrtIp, psum, bad, J, st);
+        case 32: return sqrt_t<32>(I, sqrtIp, psum, bad, J, st);
+        case 64: return sqrt_t<64>(I, sqrtIp, psum, bad, J, st);
+        case 128: return sqrt_t<128>(I, sqrtIp, psum, bad, J, st);
+        case 256: return sqrt_t<256>(I, sqrtIp, psum, bad, J, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ptycho

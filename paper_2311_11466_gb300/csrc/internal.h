@@ -1,0 +1,71 @@
+// Internal interfaces between the library's translation units (not the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace ptycho {
+
+// Arguments of the divide kernel (one cluster of CTAs per exit wave).
+struct DivideArgs {
+    float2* x;            // [J][N][N] current iterate (read in LOADX mode / as x_prev)
+    float2* y;            // [J][N][N] divide output y = P^c_D x (in: y_prev for the re-split)
+    const float* sqrtIp;  // [J][N*N] sqrt(I_j) in the kernel's frequency order
+    const float2* P;      // [N][N] probe
+    const float2* O;      // [M_rows][M_cols] object
+    const int2* pos;      // [J] (row, col)
+    const float2* tw;     // [N] stage twiddles, see divide.cu
+    double* e_part;       // [J][C] per-CTA partial of sum (|Psi| - sqrt I)^2
+    int J;
+    int Mc;               // object row stride (columns)
+    int load_x;           // 1: x_k is x[] (no re-split); 0: x_k = re-split(pa, pb)
+    float pa, pb;         // re-split coefficients of the previous iteration
+    float c;              // divide relaxation
+    int write_x;          // store x_k to x[] (needed when this iteration's a != 1)
+    int err_only;         // only the Fourier error of x_k (no y written)
+};
+
+// Supported pattern sides.
+bool divide_supported(int N);
+int divide_cluster_size(int N);
+// Twiddle table of the divide kernel for side N (host, FP64 rounded to FP32).
+void divide_twiddles(int N, std::vector<float2>& tw);
+cudaError_t divide_prepare(int N);  // one-time kernel attributes
+cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st);
+// sqrt of the intensities into the divide kernel's frequency order; flags
+// *bad (device int) if any value is negative or not finite; per-pattern sums
+// of I in FP64 into psum[J].
+cudaError_t launch_sqrt_permute(int N, const float* I, float* sqrtIp, double* psum, int* bad,
+                                int J, cudaStream_t st);
+
+// Concur step and elementwise kernels (concur.cu).
+struct ConcurBufs {
+    float2* numO;          // [M] object numerator
+    float* denO;           // [M] object denominator
+    unsigned* maxO;        // bits of max(denO) (float, >= 0)
+    float2* partP;         // [chunks][N*N] probe numerator partials
+    float* partPd;         // [chunks][N*N] probe denominator partials
+    double2* numP;         // [N*N]
+    double* denP;          // [N*N]
+    unsigned long long* maxP;  // bits of max(denP) (double, >= 0)
+    int* tile_ptr;         // [tiles + 1] CSR of positions overlapping each object tile
+    int* tile_list;
+    int tiles_r, tiles_c, chunks;
+};
+constexpr int kObjTile = 32;
+int probe_chunks(int J, int N);
+cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
+                          const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
+                          const double* e_part, int n_part, double inv_sumI, double* e_slot,
+                          int concur_mode, cudaStream_t st);
+cudaError_t launch_form_waves(float2* x, const float2* P, const float2* O, const int2* pos,
+                              int J, int N, int Mc, cudaStream_t st);
+cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, const float2* O,
+                               const int2* pos, int J, int N, int Mc, float pa, float pb,
+                               cudaStream_t st);
+cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
+                             cudaStream_t st);
+
+}  // namespace ptycho

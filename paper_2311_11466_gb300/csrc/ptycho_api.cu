@@ -1,0 +1,597 @@
+// C ABI of the library (declared in include/ptycho.h): context, scan loading,
+// the abc iteration loop, state access and error history.
+//
+// State kept on the device between iterations (lazy re-split): after
+// iteration k the context holds y_k = P^c_D x_k, the new object and probe
+// (O_{k+1}, P_{k+1}), x_k when a_k != 1, and the pending coefficients (a_k, b_k).
+// The next divide kernel forms x_{k+1} = a_k (b_k P O_j + (1 - b_k) y_k) + (1 - a_k) x_k
+// on the fly, so the re-split costs no extra pass over memory.  A caller who
+// asks for x materialises it with the identical expression.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ptycho.h"
+#include "internal.h"
+
+using namespace ptycho;
+
+namespace {
+
+constexpr int kRing = 65536;  // error-history entries kept on the device
+constexpr int kProfMax = 4096;  // iterations the timing hook can record
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ptycho_ctx {
+    ptycho_opts opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    bool loaded = false;
+    int J = 0, N = 0, Mr = 0, Mc = 0, C = 0;
+    double sumI = 0.0;
+
+    float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
+    float* sqrtIp = nullptr;
+    int2* pos = nullptr;
+    double *e_part = nullptr, *e_ring = nullptr, *e_tmp = nullptr;
+    int* dflag = nullptr;
+    ConcurBufs cb{};
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+
+    bool have_x = true;
+    float pa = 1.f, pb = 1.f;
+    int64_t iters = 0;
+
+    // measurement: three events per recorded iteration
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    int prof_n = 0;
+};
+
+namespace {
+
+int fail(ptycho_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(ptycho_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, PTYCHO_ENOMEM, m);
+    }
+    return fail(ctx, PTYCHO_ECUDA, m);
+}
+
+#define PT_CUDA(ctx, call)                                      \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <class T>
+int dalloc(ptycho_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    const size_t b = count * sizeof(T);
+    if (b == 0) return PTYCHO_OK;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PTYCHO_ENOMEM, "device allocation of " + std::to_string(b) +
+                                            " bytes failed: " + cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    ctx->bytes += b;
+    *p = static_cast<T*>(q);
+    return PTYCHO_OK;
+}
+
+void free_scan(ptycho_ctx* ctx) {
+    for (void* p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    ctx->bytes = 0;
+    ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;
+    ctx->sqrtIp = nullptr;
+    ctx->pos = nullptr;
+    ctx->e_part = ctx->e_ring = ctx->e_tmp = nullptr;
+    ctx->dflag = nullptr;
+    ctx->cb = ConcurBufs{};
+    ctx->loaded = false;
+    ctx->iters = 0;
+}
+
+bool all_finite(const float* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int materialise(ptycho_ctx* ctx) {
+    if (ctx->have_x) return PTYCHO_OK;
+    PT_CUDA(ctx, launch_materialise(ctx->x, ctx->y, ctx->P, ctx->O, ctx->pos, ctx->J, ctx->N,
+                                    ctx->Mc, ctx->pa, ctx->pb, ctx->stream));
+    ctx->have_x = true;
+    return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ptycho_default_opts(ptycho_opts* o) {
+    if (!o) return;
+    o->device = 0;
+    o->precision = PTYCHO_PREC_FP32;
+    o->concur = PTYCHO_CONCUR_DETERMINISTIC;
+    o->alpha = 1e-6f;
+    o->stream = nullptr;
+}
+
+int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return PTYCHO_EINVAL;
+    }
+    *out = nullptr;
+    ptycho_opts o;
+    ptycho_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != PTYCHO_PREC_FP32 && o.precision != PTYCHO_PREC_BF16X3) {
+        g_create_error = "unknown precision";
+        return PTYCHO_EINVAL;
+    }
+    if (o.concur != PTYCHO_CONCUR_DETERMINISTIC && o.concur != PTYCHO_CONCUR_ATOMIC) {
+        g_create_error = "unknown concur mode";
+        return PTYCHO_EINVAL;
+    }
+    if (!(o.alpha >= 0.0f) || !std::isfinite(o.alpha)) {
+        g_create_error = "alpha must be finite and >= 0";
+        return PTYCHO_EINVAL;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || o.device < 0 || o.device >= ndev) {
+        cudaGetLastError();
+        g_create_error = std::string("no such CUDA device: ") +
+                         (e != cudaSuccess ? cudaGetErrorString(e) : std::to_string(o.device));
+        return e != cudaSuccess ? PTYCHO_ECUDA : PTYCHO_EINVAL;
+    }
+    if (o.precision == PTYCHO_PREC_BF16X3) {
+        g_create_error = "BF16X3 precision is not available in this build";
+        return PTYCHO_EINVAL;
+    }
+    DeviceGuard dg(o.device);
+    ptycho_ctx* ctx = new ptycho_ctx();
+    ctx->opts = o;
+    if (o.stream) {
+        ctx->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            delete ctx;
+            return PTYCHO_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return PTYCHO_OK;
+}
+
+void ptycho_destroy(ptycho_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard dg(ctx->opts.device);
+        cudaStreamSynchronize(ctx->stream);
+        free_scan(ctx);
+        for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+const char* ptycho_last_error(const ptycho_ctx* ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, int precision) {
+    (void)precision;
+    if (J <= 0 || N <= 0 || M_rows <= 0 || M_cols <= 0) return 0;
+    const size_t NN = (size_t)N * N, M = (size_t)M_rows * M_cols;
+    const int C = divide_cluster_size(N) > 0 ? divide_cluster_size(N) : 1;
+    const size_t chunks = (size_t)probe_chunks(J, N);
+    const int tiles = ((M_rows + kObjTile - 1) / kObjTile) * ((M_cols + kObjTile - 1) / kObjTile);
+    const int tr_per = (N + kObjTile - 1) / kObjTile + 1;
+    size_t b = 0;
+    b += 2 * (size_t)J * NN * sizeof(float2);        // x, y
+    b += (size_t)J * NN * sizeof(float);             // sqrt(I)
+    b += 2 * NN * sizeof(float2) + M * sizeof(float2);  // P, tw, O
+    b += (size_t)J * sizeof(int2);
+    b += (size_t)J * C * sizeof(double) + (size_t)kRing * sizeof(double) + 64;
+    b += M * (sizeof(float2) + sizeof(float)) + 16;
+    b += chunks * NN * (sizeof(float2) + sizeof(float));
+    b += NN * (sizeof(double2) + sizeof(double));
+    b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
+    b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
+    return b;
+}
+
+int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_rc,
+                     const float* intensity, int32_t M_rows, int32_t M_cols, const float* obj0,
+                     const float* probe0, uint32_t flags) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (J < 1) return fail(ctx, PTYCHO_EINVAL, "J must be >= 1");
+    if (!divide_supported(N))
+        return fail(ctx, PTYCHO_EINVAL, "N must be one of 8, 16, 32, 64, 128, 256");
+    if (M_rows < N || M_cols < N) return fail(ctx, PTYCHO_EINVAL, "object smaller than the probe");
+    if (!pos_rc || !intensity || !obj0 || !probe0)
+        return fail(ctx, PTYCHO_EINVAL, "NULL input pointer");
+    if ((size_t)J * N * N > (size_t)1 << 40) return fail(ctx, PTYCHO_EINVAL, "scan too large");
+    for (int j = 0; j < J; ++j) {
+        const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+        if (r < 0 || r > M_rows - N || c < 0 || c > M_cols - N)
+            return fail(ctx, PTYCHO_EINVAL, "position " + std::to_string(j) + " = (" +
+                                                std::to_string(r) + ", " + std::to_string(c) +
+                                                ") outside [0, M - N]");
+    }
+    const size_t NN = (size_t)N * N, M = (size_t)M_rows * M_cols;
+    if (!all_finite(obj0, 2 * M)) return fail(ctx, PTYCHO_EINVAL, "obj0 has a non-finite value");
+    if (!all_finite(probe0, 2 * NN)) return fail(ctx, PTYCHO_EINVAL, "probe0 has a non-finite value");
+
+    DeviceGuard dg(ctx->opts.device);
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    free_scan(ctx);
+
+    // Object tiles: CSR lists of the positions whose window overlaps each tile,
+    // in ascending position order (integer work, done here).
+    const int tiles_r = (M_rows + kObjTile - 1) / kObjTile;
+    const int tiles_c = (M_cols + kObjTile - 1) / kObjTile;
+    std::vector<int> tile_cnt((size_t)tiles_r * tiles_c + 1, 0);
+    for (int j = 0; j < J; ++j) {
+        const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+        for (int ti = r / kObjTile; ti <= (r + N - 1) / kObjTile; ++ti)
+            for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
+                tile_cnt[(size_t)ti * tiles_c + tj + 1]++;
+    }
+    for (size_t t = 1; t < tile_cnt.size(); ++t) tile_cnt[t] += tile_cnt[t - 1];
+    std::vector<int> tile_list((size_t)tile_cnt.back());
+    {
+        std::vector<int> fill(tile_cnt.begin(), tile_cnt.end() - 1);
+        for (int j = 0; j < J; ++j) {
+            const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+            for (int ti = r / kObjTile; ti <= (r + N - 1) / kObjTile; ++ti)
+                for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
+                    tile_list[(size_t)fill[(size_t)ti * tiles_c + tj]++] = j;
+        }
+    }
+
+    const int C = divide_cluster_size(N);
+    const int chunks = probe_chunks(J, N);
+    const int sq_blocks = (int)((NN + 255) / 256);
+    double* psum = nullptr;
+    int rc;
+#define PT_ALLOC(p, n)                           \
+    do {                                         \
+        if ((rc = dalloc(ctx, &(p), (n))) != 0) { \
+            free_scan(ctx);                      \
+            return rc;                           \
+        }                                        \
+    } while (0)
+    PT_ALLOC(ctx->x, (size_t)J * NN);
+    PT_ALLOC(ctx->y, (size_t)J * NN);
+    PT_ALLOC(ctx->sqrtIp, (size_t)J * NN);
+    PT_ALLOC(ctx->P, NN);
+    PT_ALLOC(ctx->tw, (size_t)N);
+    PT_ALLOC(ctx->O, M);
+    PT_ALLOC(ctx->pos, (size_t)J);
+    PT_ALLOC(ctx->e_part, (size_t)J * C);
+    PT_ALLOC(ctx->e_ring, (size_t)kRing);
+    PT_ALLOC(ctx->e_tmp, (size_t)4);
+    PT_ALLOC(ctx->dflag, (size_t)4);
+    PT_ALLOC(ctx->cb.numO, M);
+    PT_ALLOC(ctx->cb.denO, M);
+    PT_ALLOC(ctx->cb.maxO, (size_t)1);
+    PT_ALLOC(ctx->cb.partP, (size_t)chunks * NN);
+    PT_ALLOC(ctx->cb.partPd, (size_t)chunks * NN);
+    PT_ALLOC(ctx->cb.numP, NN);
+    PT_ALLOC(ctx->cb.denP, NN);
+    PT_ALLOC(ctx->cb.maxP, (size_t)1);
+    PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
+    PT_ALLOC(ctx->cb.tile_list, tile_list.size() > 0 ? tile_list.size() : 1);
+    PT_ALLOC(psum, (size_t)J * sq_blocks);
+#undef PT_ALLOC
+    ctx->cb.tiles_r = tiles_r;
+    ctx->cb.tiles_c = tiles_c;
+    ctx->cb.chunks = chunks;
+    ctx->J = J;
+    ctx->N = N;
+    ctx->Mr = M_rows;
+    ctx->Mc = M_cols;
+    ctx->C = C;
+
+    std::vector<float2> tw;
+    divide_twiddles(N, tw);
+    cudaStream_t st = ctx->stream;
+    auto bail = [&](cudaError_t e, const char* where) {
+        int r = cuda_fail(ctx, e, where);
+        cudaStreamSynchronize(st);
+        free_scan(ctx);
+        return r;
+    };
+    cudaError_t e;
+#define PT_STEP(call)                                   \
+    do {                                                \
+        if ((e = (call)) != cudaSuccess) return bail(e, #call); \
+    } while (0)
+    PT_STEP(divide_prepare(N));
+    PT_STEP(cudaMemcpyAsync(ctx->tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PT_STEP(cudaMemcpyAsync(ctx->pos, pos_rc, (size_t)J * sizeof(int2), cudaMemcpyHostToDevice, st));
+    PT_STEP(cudaMemcpyAsync(ctx->O, obj0, M * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PT_STEP(cudaMemcpyAsync(ctx->P, probe0, NN * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PT_STEP(cudaMemcpyAsync(ctx->cb.tile_ptr, tile_cnt.data(), tile_cnt.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, st));
+    if (!tile_list.empty())
+        PT_STEP(cudaMemcpyAsync(ctx->cb.tile_list, tile_list.data(), tile_list.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, st));
+    PT_STEP(cudaMemsetAsync(ctx->dflag, 0, 4 * sizeof(int), st));
+    PT_STEP(cudaMemsetAsync(ctx->cb.maxO, 0, sizeof(unsigned), st));
+    PT_STEP(cudaMemsetAsync(ctx->cb.maxP, 0, sizeof(unsigned long long), st));
+    // The intensities pass through the y buffer (twice their size) on their way
+    // to the permuted sqrt(I) layout.
+    const float* Idev = intensity;
+    if (!(flags & PTYCHO_LOAD_INTENSITY_DEVICE)) {
+        PT_STEP(cudaMemcpyAsync(ctx->y, intensity, (size_t)J * NN * sizeof(float),
+                                cudaMemcpyHostToDevice, st));
+        Idev = reinterpret_cast<const float*>(ctx->y);
+    }
+    PT_STEP(launch_sqrt_permute(N, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
+    PT_STEP(launch_form_waves(ctx->x, ctx->P, ctx->O, ctx->pos, J, N, M_cols, st));
+    std::vector<double> hsum((size_t)J * sq_blocks);
+    int bad = 0;
+    PT_STEP(cudaMemcpyAsync(hsum.data(), psum, hsum.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PT_STEP(cudaMemcpyAsync(&bad, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PT_STEP(cudaStreamSynchronize(st));
+#undef PT_STEP
+    if (bad) {
+        free_scan(ctx);
+        return fail(ctx, PTYCHO_EINVAL, "intensity has a negative or non-finite value");
+    }
+    double s = 0.0;
+    for (double v : hsum) s += v;
+    ctx->sumI = s;
+    ctx->loaded = true;
+    ctx->have_x = true;
+    ctx->pa = ctx->pb = 1.f;
+    ctx->iters = 0;
+    return PTYCHO_OK;
+}
+
+int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
+        return fail(ctx, PTYCHO_EINVAL, "a, b, c must be finite");
+    if (n_iter < 0) return fail(ctx, PTYCHO_EINVAL, "n_iter must be >= 0");
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    DeviceGuard dg(ctx->opts.device);
+    const double inv_sumI = ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0;
+    for (int it = 0; it < n_iter; ++it) {
+        DivideArgs da{};
+        da.x = ctx->x;
+        da.y = ctx->y;
+        da.sqrtIp = ctx->sqrtIp;
+        da.P = ctx->P;
+        da.O = ctx->O;
+        da.pos = ctx->pos;
+        da.tw = ctx->tw;
+        da.e_part = ctx->e_part;
+        da.J = ctx->J;
+        da.Mc = ctx->Mc;
+        da.load_x = ctx->have_x ? 1 : 0;
+        da.pa = ctx->pa;
+        da.pb = ctx->pb;
+        da.c = c;
+        da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;
+        da.err_only = 0;
+        const bool rec = ctx->prof && ctx->prof_n < kProfMax;
+        if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
+        PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+        if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 1], ctx->stream));
+        double* slot = ctx->e_ring + (ctx->iters % kRing);
+        PT_CUDA(ctx, launch_concur(ctx->y, ctx->P, ctx->O, ctx->pos, ctx->cb, ctx->J, ctx->N,
+                                   ctx->Mr, ctx->Mc, ctx->opts.alpha, ctx->e_part,
+                                   ctx->J * ctx->C, inv_sumI, slot, ctx->opts.concur, ctx->stream));
+        if (rec) {
+            PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 2], ctx->stream));
+            ctx->prof_n++;
+        }
+        ctx->have_x = false;
+        ctx->pa = a;
+        ctx->pb = b;
+        ctx->iters++;
+    }
+    return PTYCHO_OK;
+}
+
+int ptycho_get_object_probe(ptycho_ctx* ctx, float* obj_out, float* probe_out) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    DeviceGuard dg(ctx->opts.device);
+    if (obj_out)
+        PT_CUDA(ctx, cudaMemcpyAsync(obj_out, ctx->O, (size_t)ctx->Mr * ctx->Mc * sizeof(float2),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    if (probe_out)
+        PT_CUDA(ctx, cudaMemcpyAsync(probe_out, ctx->P, (size_t)ctx->N * ctx->N * sizeof(float2),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PTYCHO_OK;
+}
+
+int ptycho_set_object_probe(ptycho_ctx* ctx, const float* obj, const float* probe) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    const size_t M = (size_t)ctx->Mr * ctx->Mc, NN = (size_t)ctx->N * ctx->N;
+    if (obj && !all_finite(obj, 2 * M)) return fail(ctx, PTYCHO_EINVAL, "object has a non-finite value");
+    if (probe && !all_finite(probe, 2 * NN)) return fail(ctx, PTYCHO_EINVAL, "probe has a non-finite value");
+    DeviceGuard dg(ctx->opts.device);
+    // the pending re-split uses the object and probe: fix x first
+    int rc = materialise(ctx);
+    if (rc) return rc;
+    if (obj)
+        PT_CUDA(ctx, cudaMemcpyAsync(ctx->O, obj, M * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    if (probe)
+        PT_CUDA(ctx, cudaMemcpyAsync(ctx->P, probe, NN * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PTYCHO_OK;
+}
+
+int ptycho_get_exit_waves(ptycho_ctx* ctx, float* x_out) {
+    if (!ctx || !x_out) return ctx ? fail(ctx, PTYCHO_EINVAL, "x_out is NULL") : PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    DeviceGuard dg(ctx->opts.device);
+    int rc = materialise(ctx);
+    if (rc) return rc;
+    PT_CUDA(ctx, cudaMemcpyAsync(x_out, ctx->x, (size_t)ctx->J * ctx->N * ctx->N * sizeof(float2),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PTYCHO_OK;
+}
+
+int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* x) {
+    if (!ctx || !x) return ctx ? fail(ctx, PTYCHO_EINVAL, "x is NULL") : PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    const size_t n = (size_t)ctx->J * ctx->N * ctx->N;
+    if (!all_finite(x, 2 * n)) return fail(ctx, PTYCHO_EINVAL, "x has a non-finite value");
+    DeviceGuard dg(ctx->opts.device);
+    PT_CUDA(ctx, cudaMemcpyAsync(ctx->x, x, n * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->have_x = true;
+    ctx->pa = ctx->pb = 1.f;
+    return PTYCHO_OK;
+}
+
+int ptycho_errors(ptycho_ctx* ctx, double* fourier_err, int32_t cap, int32_t* n_written) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (cap < 0 || (cap > 0 && !fourier_err) || !n_written)
+        return fail(ctx, PTYCHO_EINVAL, "bad output buffer");
+    *n_written = 0;
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    DeviceGuard dg(ctx->opts.device);
+    const int64_t have = ctx->iters < kRing ? ctx->iters : kRing;
+    const int64_t first = ctx->iters - have;  // oldest kept iteration
+    const int32_t n = (int32_t)(have < cap ? have : cap);
+    std::vector<double> ring((size_t)(have > 0 ? kRing : 0));
+    if (have > 0) {
+        PT_CUDA(ctx, cudaMemcpyAsync(ring.data(), ctx->e_ring, (size_t)kRing * sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int32_t i = 0; i < n; ++i) fourier_err[i] = ring[(size_t)((first + i) % kRing)];
+    *n_written = n;
+    return PTYCHO_OK;
+}
+
+int64_t ptycho_iteration_count(const ptycho_ctx* ctx) { return ctx && ctx->loaded ? ctx->iters : 0; }
+
+int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
+    if (!ctx || !fourier_err) return ctx ? fail(ctx, PTYCHO_EINVAL, "NULL output") : PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    DeviceGuard dg(ctx->opts.device);
+    DivideArgs da{};
+    da.x = ctx->x;
+    da.y = ctx->y;
+    da.sqrtIp = ctx->sqrtIp;
+    da.P = ctx->P;
+    da.O = ctx->O;
+    da.pos = ctx->pos;
+    da.tw = ctx->tw;
+    da.e_part = ctx->e_part;
+    da.J = ctx->J;
+    da.Mc = ctx->Mc;
+    da.load_x = 0;
+    da.pa = 1.f;
+    da.pb = 1.f;
+    da.c = 1.f;
+    da.write_x = 0;
+    da.err_only = 1;
+    PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+    PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->J * ctx->C, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
+                                  ctx->e_tmp, ctx->stream));
+    PT_CUDA(ctx, cudaMemcpyAsync(fourier_err, ctx->e_tmp, sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PTYCHO_OK;
+}
+
+size_t ptycho_device_bytes(const ptycho_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+int ptycho_profile_enable(ptycho_ctx* ctx, int enable) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    DeviceGuard dg(ctx->opts.device);
+    if (enable) {
+        while (ctx->ev.size() < (size_t)3 * kProfMax) {
+            cudaEvent_t e;
+            PT_CUDA(ctx, cudaEventCreate(&e));
+            ctx->ev.push_back(e);
+        }
+        ctx->prof_n = 0;
+    }
+    ctx->prof = enable != 0;
+    return PTYCHO_OK;
+}
+
+int ptycho_profile_read(ptycho_ctx* ctx, double* divide_ms, double* concur_ms, int32_t* n_iters) {
+    if (!ctx || !divide_ms || !concur_ms || !n_iters) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    DeviceGuard dg(ctx->opts.device);
+    PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double d = 0.0, c = 0.0;
+    for (int i = 0; i < ctx->prof_n; ++i) {
+        float a = 0.f, b = 0.f;
+        PT_CUDA(ctx, cudaEventElapsedTime(&a, ctx->ev[3 * i], ctx->ev[3 * i + 1]));
+        PT_CUDA(ctx, cudaEventElapsedTime(&b, ctx->ev[3 * i + 1], ctx->ev[3 * i + 2]));
+        d += a;
+        c += b;
+    }
+    *divide_ms = d;
+    *concur_ms = c;
+    *n_iters = ctx->prof_n;
+    return PTYCHO_OK;
+}
+
+}  // extern "C"
