@@ -193,7 +193,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "precision", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "medium", "tiny"])
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -220,7 +220,8 @@ def main():
 
     scan = synth.make_scan(spec)
     J, N = scan.J, scan.N
-    stream = torch.cuda.current_stream(local)
+    # one dedicated stream for the library and for the timing events
+    stream = torch.cuda.Stream(device=local)
     r = native.Reconstruction(device=local, stream=stream.cuda_stream)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
     r.iterate(*RAAR, args.warmup)
@@ -267,7 +268,7 @@ def main():
     O_h, P_h = pin(scan.obj0), pin(scan.probe0)
     O_out = pin(np.empty(scan.M_shape, dtype=np.complex64))
     P_out = pin(np.empty((N, N), dtype=np.complex64))
-    e2e_iters = args.e2e_iters
+    e2e_iters = max(args.e2e_iters, 1)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()

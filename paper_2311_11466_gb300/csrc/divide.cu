@@ -7,19 +7,23 @@
 //   e_j  = sum_q (|Psi| - sqrt(I_j))^2
 //
 // One thread-block cluster of C CTAs owns one N x N exit wave; CTA c holds
-// R = N / C consecutive rows in shared memory (FP32 complex).  The 2-D DFT is
-// a row DFT, a cluster-wide transpose through distributed shared memory, and
-// a second row DFT; every 1-D DFT of length N = A * B runs as two in-register
-// radix passes (length A over stride-B elements, a twiddle, length B across
-// threads) in place in shared memory.  The spectrum therefore sits in a
-// digit-permuted order; sqrt(I) is stored in that same order at load time so
-// the modulus step reads it with contiguous vector loads.
+// R = N / C consecutive rows in shared memory (FP32 complex).  Every 1-D DFT
+// of length N = A * B runs as two in-register passes in place in shared
+// memory: pass 1 takes the A elements t + B e (e < A) of one thread, a DFT of
+// length A and the twiddle W_N^{t k}; pass 2 takes the B elements of one k, a
+// DFT of length B.  The spectrum is left in that digit-permuted order (the
+// sqrt(I) array is stored in the same order at load time).
 //
-// Shared-memory row layout: the element of 1-D index t + B e (t < B, e < A)
-// lives at slot e (B + 1) + t, so stage-1 threads (fixed e across lanes) and
-// stage-2 threads (contiguous runs of B) are both bank-conflict free; the row
-// stride RS is congruent to 9 mod 16 complex so column-wise transposes are
-// conflict free as well.
+// The row DFT's second pass pushes its outputs straight into the CTA that
+// owns their column frequencies (distributed shared memory stores), so the
+// transpose costs no pass of its own; the inverse column pass pushes back the
+// same way.  Each push is bracketed by two cluster barriers: all CTAs finish
+// reading the slots about to be overwritten, then all pushes land before the
+// next pass reads them.  Four cluster barriers per exit wave.
+//
+// Shared-memory row layout: element t + B e of a row lives at slot e (B + 1) + t
+// so both passes read conflict-free; the row stride RS makes the passes whose
+// lanes run over rows conflict-free as well.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -33,31 +37,31 @@ namespace ptycho {
 namespace {
 
 template <int N> struct Cfg;
-template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 64; };
-template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64; };
-template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128; };
-template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256; };
-template <> struct Cfg<128> { static constexpr int A = 16, B = 8,  C = 4, T = 256; };
-template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 8, T = 256; };
+// A x B radix split, cluster size C, threads T, row stride residue RSM (mod
+// 16), and the CTAs per SM the register budget is sized for (MINB).
+template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 32,  RSM = 9, MINB = 4; };
+template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64,  RSM = 9, MINB = 4; };
+template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
+template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256, RSM = 9, MINB = 4; };
+template <> struct Cfg<128> { static constexpr int A = 8,  B = 16, C = 4, T = 256, RSM = 9, MINB = 3; };
+template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 8, T = 512, RSM = 1, MINB = 2; };
 
 template <int N>
 struct Geo {
     static constexpr int A = Cfg<N>::A, B = Cfg<N>::B, C = Cfg<N>::C, T = Cfg<N>::T;
     static constexpr int R = N / C;       // rows per CTA
-    static constexpr int KC = A / C;      // stage-2 indices (k1) owned per CTA after the transpose
+    static constexpr int KC = A / C;      // pass-2 indices k owned per CTA after the transpose
     static constexpr int RS0 = A * (B + 1);
-    static constexpr int RS = RS0 + ((9 - RS0 % 16) + 16) % 16;  // row stride, = 9 mod 16
-    static constexpr int PER = R * R / T;  // transpose elements per thread per partner block
-    static constexpr int GT = C < 4 ? C : 4;  // partner blocks exchanged per cluster barrier
-    static constexpr size_t SMEM = (size_t)R * RS * sizeof(float2) + N * sizeof(float2) +
+    static constexpr int RS = RS0 + ((Cfg<N>::RSM - RS0 % 16) + 16) % 16;  // row stride
+    static constexpr int TP2 = (R * A + T - 1) / T;  // pass-2 tasks per thread
+    static constexpr int TP5 = (R * B + T - 1) / T;  // inverse column pass-1 tasks per thread
+    static constexpr size_t SMEM = (size_t)R * RS * sizeof(float2) + 2 * N * sizeof(float2) +
                                    32 * sizeof(double);
     static_assert(A * B == N, "radix split");
     static_assert(A % C == 0, "cluster split");
-    static_assert((R * R) % T == 0, "transpose split");
-    static_assert(C % GT == 0, "exchange rounds");
 };
 
-// Slot of the spectral index with stage-2 index k (= k1) and stage-2 output k2.
+// Slot of the spectral index q of CTA cta (pass-2 index k = cta KC + q / B, output q % B).
 template <int N>
 __device__ __forceinline__ int slot_freq(int cta, int q) {
     using G = Geo<N>;
@@ -70,68 +74,27 @@ __device__ __forceinline__ int slot_space(int r) {
     return (r / G::B) * (G::B + 1) + r % G::B;
 }
 
-// Cluster-wide transpose.  FWD: rows (spatial) x spectral slots  ->  this
-// CTA's spectral indices x all spatial rows.  !FWD: the reverse.  Partner
-// blocks are exchanged in rounds (partner = rank XOR d): read the partner's
-// block into registers, cluster barrier, overwrite the same block locally;
-// the partner reads exactly the block this CTA overwrites in the same round.
-template <int N, bool FWD>
-__device__ __forceinline__ void exchange(float2* buf, cg::cluster_group& cl, int c) {
-    using G = Geo<N>;
-    constexpr int R = G::R, RS = G::RS, T = G::T, PER = G::PER, GT = G::GT, C = G::C;
-#pragma unroll 1
-    for (int g = 0; g < C; g += GT) {
-        float2 reg[GT][PER];
-#pragma unroll
-        for (int d = 0; d < GT; ++d) {
-            const int p = c ^ (g + d);
-            const float2* src = cl.map_shared_rank(buf, p);
-#pragma unroll
-            for (int m = 0; m < PER; ++m) {
-                const int e = threadIdx.x + T * m;
-                if (FWD) {
-                    const int q = e % R, i = e / R;
-                    reg[d][m] = src[i * RS + slot_freq<N>(c, q)];
-                } else {
-                    const int i = e % R, q = e / R;
-                    reg[d][m] = src[q * RS + slot_space<N>(R * c + i)];
-                }
-            }
-        }
-        cl.sync();
-#pragma unroll
-        for (int d = 0; d < GT; ++d) {
-            const int p = c ^ (g + d);
-#pragma unroll
-            for (int m = 0; m < PER; ++m) {
-                const int e = threadIdx.x + T * m;
-                if (FWD) {
-                    const int q = e % R, i = e / R;
-                    buf[q * RS + slot_space<N>(R * p + i)] = reg[d][m];
-                } else {
-                    const int i = e % R, q = e / R;
-                    buf[i * RS + slot_freq<N>(p, q)] = reg[d][m];
-                }
-            }
-        }
-    }
-}
-
 template <int N, bool ERR_ONLY>
-__global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args) {
+__global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const DivideArgs args) {
     using G = Geo<N>;
-    constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS;
+    constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS, KC = G::KC;
+    constexpr int TP2 = G::TP2, TP5 = G::TP5;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = buf + R * RS;
-    double* red = reinterpret_cast<double*>(tw + N);
+    float2* twA = buf + R * RS;   // twA[k B + t] = W_N^{t k}
+    float2* twB = twA + N;        // twB[t A + k] = W_N^{t k}
+    double* red = reinterpret_cast<double*>(twB + N);
 
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
     const int j = blockIdx.x / C;
     const int tid = threadIdx.x;
 
-    for (int i = tid; i < N; i += T) tw[i] = args.tw[i];
+    for (int i = tid; i < N; i += T) {
+        const float2 w = args.tw[i];
+        twA[i] = w;
+        twB[(i % B) * A + i / B] = w;
+    }
     __syncthreads();
 
     const int2 s = args.pos[j];
@@ -140,7 +103,7 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
     const bool load_x = args.load_x != 0, write_x = args.write_x != 0;
     const bool need_y = args.pb != 1.0f, need_xp = args.pa != 1.0f;
 
-    // Phase 1: form x_k and run the row DFT's first pass.
+    // Phase 1: form x_k, row DFT pass 1 (lanes over t).
 #pragma unroll 1
     for (int task = tid; task < R * B; task += T) {
         const int row = task / B, t = task % B;
@@ -154,7 +117,7 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
             if (load_x) {
                 xv = args.x[idx];
             } else {
-                const float2 z = cmul_rn(args.P[r * N + n], Ow[(size_t)r * args.Mc + n]);
+                const float2 z = cmul_rn(__ldg(args.P + r * N + n), __ldg(Ow + (size_t)r * args.Mc + n));
                 const float2 yv = need_y ? args.y[idx] : make_float2(0.f, 0.f);
                 const float2 xp = need_xp ? args.x[idx] : make_float2(0.f, 0.f);
                 xv = resplit_rn(z, yv, xp, args.pa, args.pb);
@@ -164,27 +127,42 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
         }
         dft_reg<A, false>(v);
 #pragma unroll
-        for (int k = 0; k < A; ++k) buf[row * RS + k * (B + 1) + t] = cmul(v[k], tw[k * B + t]);
+        for (int k = 0; k < A; ++k) buf[row * RS + k * (B + 1) + t] = cmul(v[k], twA[k * B + t]);
     }
     __syncthreads();
 
-    // Phase 2: row DFT second pass (frequency k1 + A k2 -> slot (k2, k1)).
-#pragma unroll 1
-    for (int task = tid; task < R * A; task += T) {
-        const int row = task / A, k = task % A;
-        float2* p = buf + row * RS + k * (B + 1);
-        float2 u[B];
+    // Phase 2: row DFT pass 2 (lanes over rows), pushed transposed to the CTA
+    // owning each column frequency.
+    {
+        float2 u[TP2][B];
 #pragma unroll
-        for (int t = 0; t < B; ++t) u[t] = p[t];
-        dft_reg<B, false>(u);
+        for (int i = 0; i < TP2; ++i) {
+            const int task = tid + i * T;
+            if (task < R * A) {
+                const int k = task / R, row = task % R;
+                const float2* p = buf + row * RS + k * (B + 1);
 #pragma unroll
-        for (int t = 0; t < B; ++t) p[t] = u[t];
+                for (int t = 0; t < B; ++t) u[i][t] = p[t];
+            }
+        }
+        cl.sync();
+#pragma unroll
+        for (int i = 0; i < TP2; ++i) {
+            const int task = tid + i * T;
+            if (task < R * A) {
+                const int k = task / R, row = task % R;
+                dft_reg<B, false>(u[i]);
+                const int owner = k / KC;
+                float2* dst = cl.map_shared_rank(buf, owner) +
+                              ((k - owner * KC) * B) * RS + slot_space<N>(c * R + row);
+#pragma unroll
+                for (int q = 0; q < B; ++q) dst[q * RS] = u[i][q];
+            }
+        }
+        cl.sync();
     }
-    cl.sync();
-    exchange<N, true>(buf, cl, c);
-    __syncthreads();
 
-    // Phase 3: column DFT first pass (rows now hold whole columns).
+    // Phase 3: column DFT pass 1 (rows now hold whole columns; lanes over t).
 #pragma unroll 1
     for (int task = tid; task < R * B; task += T) {
         const int row = task / B, t = task % B;
@@ -194,12 +172,13 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
         for (int e = 0; e < A; ++e) v[e] = p[e * (B + 1)];
         dft_reg<A, false>(v);
 #pragma unroll
-        for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], tw[k * B + t]);
+        for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], twA[k * B + t]);
     }
     __syncthreads();
 
-    // Phase 4: column DFT second pass, Fourier-modulus projection with the
-    // c relaxation and the 1/N^2 of the inverse, inverse second pass.
+    // Phase 4: column DFT pass 2, Fourier-modulus projection with the c
+    // relaxation and the 1/N^2 of the inverse, inverse pass 2 and conjugate
+    // twiddle (lanes over k).
     float err = 0.f;
     const float* sq = args.sqrtIp + pat + (size_t)c * R * N;
     const float inv_n2 = 1.0f / (float)(N * N);
@@ -217,7 +196,7 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
         if constexpr (B % 4 == 0) {
 #pragma unroll
             for (int q = 0; q < B; q += 4) {
-                const float4 f = *reinterpret_cast<const float4*>(sp + q);
+                const float4 f = __ldcs(reinterpret_cast<const float4*>(sp + q));
                 sv[q] = f.x; sv[q + 1] = f.y; sv[q + 2] = f.z; sv[q + 3] = f.w;
             }
         } else {
@@ -244,29 +223,46 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
         if constexpr (!ERR_ONLY) {
             dft_reg<B, true>(u);
 #pragma unroll
-            for (int t = 0; t < B; ++t) p[t] = cconjmul(tw[k * B + t], u[t]);
+            for (int t = 0; t < B; ++t) p[t] = cconjmul(twB[t * A + k], u[t]);
         }
     }
 
     if constexpr (!ERR_ONLY) {
         __syncthreads();
-        // Phase 5: column inverse first pass (natural spatial order).
-#pragma unroll 1
-        for (int task = tid; task < R * B; task += T) {
-            const int row = task / B, t = task % B;
-            float2* p = buf + row * RS + t;
-            float2 v[A];
+        // Phase 5: column inverse pass 1 (lanes over the local rows), pushed
+        // back to the CTA owning each spatial row.
+        {
+            float2 v[TP5][A];
 #pragma unroll
-            for (int k = 0; k < A; ++k) v[k] = p[k * (B + 1)];
-            dft_reg<A, true>(v);
+            for (int i = 0; i < TP5; ++i) {
+                const int task = tid + i * T;
+                if (task < R * B) {
+                    const int t = task / R, rho = task % R;
+                    const float2* p = buf + rho * RS + t;
 #pragma unroll
-            for (int e = 0; e < A; ++e) p[e * (B + 1)] = v[e];
+                    for (int k = 0; k < A; ++k) v[i][k] = p[k * (B + 1)];
+                }
+            }
+            cl.sync();
+#pragma unroll
+            for (int i = 0; i < TP5; ++i) {
+                const int task = tid + i * T;
+                if (task < R * B) {
+                    const int t = task / R, rho = task % R;
+                    dft_reg<A, true>(v[i]);
+                    const int sf = slot_freq<N>(c, rho);
+#pragma unroll
+                    for (int e = 0; e < A; ++e) {
+                        const int r = t + B * e;
+                        float2* dst = cl.map_shared_rank(buf, r / R);
+                        dst[(r % R) * RS + sf] = v[i][e];
+                    }
+                }
+            }
+            cl.sync();
         }
-        cl.sync();
-        exchange<N, false>(buf, cl, c);
-        __syncthreads();
 
-        // Phase 6: row inverse second pass with the conjugate twiddle.
+        // Phase 6: row inverse pass 2 with the conjugate twiddle (lanes over k).
 #pragma unroll 1
         for (int task = tid; task < R * A; task += T) {
             const int row = task / A, k = task % A;
@@ -276,11 +272,11 @@ __global__ void __launch_bounds__(Geo<N>::T) divide_kernel(const DivideArgs args
             for (int t = 0; t < B; ++t) u[t] = p[t];
             dft_reg<B, true>(u);
 #pragma unroll
-            for (int t = 0; t < B; ++t) p[t] = cconjmul(tw[k * B + t], u[t]);
+            for (int t = 0; t < B; ++t) p[t] = cconjmul(twB[t * A + k], u[t]);
         }
         __syncthreads();
 
-        // Phase 7: row inverse first pass, store y_k.
+        // Phase 7: row inverse pass 1, store y_k (lanes over t).
 #pragma unroll 1
         for (int task = tid; task < R * B; task += T) {
             const int row = task / B, t = task % B;

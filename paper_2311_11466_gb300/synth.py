@@ -194,7 +194,8 @@ def make_scan(spec: ScanSpec, with_data: bool = True) -> Scan:
 # Named workloads.  "tiny": 8x8 raster of 64x64 patterns on a 176x176 object,
 # noiseless; "large": 32x32 raster of 256x256 patterns on a 1300x1300 object,
 # Poisson 1e6 photons; "precision": 64x64 raster of 256x256 patterns on a
-# 2296x2296 object, same probe and noise as "large".
+# 2296x2296 object, same probe and noise as "large"; "medium": the 16x16
+# raster version of "large" (a small case of the same kernels for profiling).
 NAMED = {
     "tiny": ScanSpec(N=64, ny=8, nx=8, step=16, jitter=2, M_rows=176, M_cols=176,
                      radius=16.0, defocus=0.02, photons=None, seed=0),
@@ -202,6 +203,8 @@ NAMED = {
                       radius=64.0, defocus=0.00125, photons=1e6, seed=1),
     "precision": ScanSpec(N=256, ny=64, nx=64, step=32, jitter=4, M_rows=2296, M_cols=2296,
                           radius=64.0, defocus=0.00125, photons=1e6, seed=3),
+    "medium": ScanSpec(N=256, ny=16, nx=16, step=32, jitter=4, M_rows=780, M_cols=780,
+                       radius=64.0, defocus=0.00125, photons=1e6, seed=5),
 }
 
 
