@@ -156,6 +156,38 @@ int ptycho_profile_enable(ptycho_ctx* ctx, int enable);
  * number of iterations recorded.  Synchronises.  Errors: EINVAL, ECUDA. */
 int ptycho_profile_read(ptycho_ctx* ctx, double* divide_ms, double* concur_ms, int32_t* n_iters);
 
+/* Probe update of the concur step with no device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, for example code whose device memory is all owned
+ * by its own allocator or pool, or a pipeline that must not allocate once it
+ * is running (an allocation there may fail, fragment a pool sized in advance,
+ * or stall the device).  It computes, from caller-provided device buffers,
+ *     P(r) = sum_j conj(O(s_j + r)) y_j(r) / (sum_j |O(s_j + r)|^2 + alpha max_r(.))
+ * (a regularised denominator of exactly 0 gives 0), the same probe update as
+ * the concur step of ptycho_iterate, with the same FP32 partial sums over
+ * fixed chunks of positions and FP64 final sums.
+ *   y          device complex float32 [J][N][N] (the divided exit waves)
+ *   obj        device complex float32 [M_rows][M_cols] (the object)
+ *   pos_rc     device int32 [J][2] (row, col) window corners
+ *   alpha      regulariser, finite, >= 0
+ *   probe_out  device complex float32 [N][N], written on success only
+ *   stream     cudaStream_t to run on (NULL: the default stream)
+ * All buffers stay owned by the caller.  Scratch lives in one static
+ * __device__ array of 7.5 MiB that every GPU loading the library holds until
+ * the process exits; it bounds N to 256.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device current),
+ * so make that first call before any stream capture.  Every call reuses the
+ * same array (the maximum and the status word are cleared at the start of
+ * each call): calls whose work overlaps on the GPU race and must not be made.
+ * Synchronises the stream before returning (to read the status word).
+ * Errors: EINVAL (NULL pointer, J < 1, N < 1 or N > 256, M_rows or M_cols
+ * < N, bad alpha, or a position whose window leaves the object: such windows
+ * are skipped on the device, probe_out is left untouched), ECUDA. */
+int ptycho_probe_update_noalloc(const float* y, const float* obj, const int32_t* pos_rc,
+                                int32_t J, int32_t N, int32_t M_rows, int32_t M_cols,
+                                float alpha, float* probe_out, void* stream);
+
 /* Bytes of device memory the context holds for its current scan. */
 size_t ptycho_device_bytes(const ptycho_ctx* ctx);
 

@@ -83,6 +83,9 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int32)]),
     "ptycho_scan_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int]),
+    "ptycho_probe_update_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                                   _P, _P]),
 }
 
 
@@ -218,6 +221,15 @@ def ptycho_profile_read(h) -> tuple[float, float, int]:
 
 def ptycho_scan_bytes(J: int, N: int, M_rows: int, M_cols: int, precision: int = 0) -> int:
     return int(lib().ptycho_scan_bytes(J, N, M_rows, M_cols, precision))
+
+
+def ptycho_probe_update_noalloc(y_dev: int, obj_dev: int, pos_dev: int, J: int, N: int,
+                                M_rows: int, M_cols: int, alpha: float, probe_out_dev: int,
+                                stream: int | None = None) -> int:
+    """Probe update from device pointers with no device allocation; returns the
+    status code (PTYCHO_OK on success) instead of raising."""
+    return int(lib().ptycho_probe_update_noalloc(y_dev, obj_dev, pos_dev, J, N, M_rows, M_cols,
+                                                 alpha, probe_out_dev, stream))
 
 
 # --- convenience wrapper ---------------------------------------------------
