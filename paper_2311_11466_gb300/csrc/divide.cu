@@ -61,6 +61,11 @@ struct Geo {
     static_assert(A % C == 0, "cluster split");
 };
 
+// True when passes 1 and 2 of a row DFT run on the same 16 lanes (A == B == 16
+// and one task per thread), so the hand-over between them is warp-local.
+template <int N>
+constexpr bool kRowPerHalfWarp = Geo<N>::A == 16 && Geo<N>::B == 16 && Geo<N>::R * 16 == Geo<N>::T;
+
 // Slot of the spectral index q of CTA cta (pass-2 index k = cta KC + q / B, output q % B).
 template <int N>
 __device__ __forceinline__ int slot_freq(int cta, int q) {
@@ -72,6 +77,12 @@ template <int N>
 __device__ __forceinline__ int slot_space(int r) {
     using G = Geo<N>;
     return (r / G::B) * (G::B + 1) + r % G::B;
+}
+
+// One bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16); it does not wait and brings nothing into the SM.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <int N, bool ERR_ONLY>
@@ -89,6 +100,16 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     const int c = (int)cl.block_rank();
     const int j = blockIdx.x / C;
     const int tid = threadIdx.x;
+
+    // Start streaming this CTA's rows of x, y and sqrt(I) into L2 at once, so
+    // the scattered per-thread loads below meet lines already on their way.
+    if (tid == 0) {
+        const size_t off = (size_t)j * N * N + (size_t)c * R * N;
+        constexpr unsigned cbytes = (unsigned)(R * N * sizeof(float2));
+        if (args.load_x || args.pa != 1.0f) prefetch_l2(args.x + off, cbytes);
+        if (!args.load_x && args.pb != 1.0f) prefetch_l2(args.y + off, cbytes);
+        prefetch_l2(args.sqrtIp + off, (unsigned)(R * N * sizeof(float)));
+    }
 
     for (int i = tid; i < N; i += T) {
         const float2 w = args.tw[i];
@@ -174,7 +195,9 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
         for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], twA[k * B + t]);
     }
-    __syncthreads();
+    // With A == B and one task per thread, the 16 lanes that wrote a row in
+    // pass 1 are the ones that read it in pass 2: a warp barrier suffices.
+    if constexpr (kRowPerHalfWarp<N>) __syncwarp(); else __syncthreads();
 
     // Phase 4: column DFT pass 2, Fourier-modulus projection with the c
     // relaxation and the 1/N^2 of the inverse, inverse pass 2 and conjugate
@@ -205,19 +228,16 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         }
 #pragma unroll
         for (int q = 0; q < B; ++q) {
+            // |Psi| and Psi/|Psi| from one reciprocal square root
             const float m2 = cabs2(u[q]);
-            const float mag = sqrtf(m2);
-            const float d = mag - sv[q];
+            const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+            const float d = fmaf(m2, rs, -sv[q]);
             err = fmaf(d, d, err);
             if constexpr (!ERR_ONLY) {
-                float2 pr;
-                if (m2 > 0.f) {
-                    pr = cscale(u[q], sv[q] / mag);
-                } else {
-                    pr = make_float2(sv[q], 0.f);
-                }
-                u[q] = make_float2(fmaf(cr, pr.x, oc * u[q].x) * inv_n2,
-                                   fmaf(cr, pr.y, oc * u[q].y) * inv_n2);
+                // c sqrt(I) Psi/|Psi| + (1 - c) Psi, scaled by 1/N^2; sqrt(I) + 0i where Psi = 0
+                const float g = (cr * sv[q]) * rs + oc;
+                u[q] = m2 > 0.f ? make_float2(u[q].x * (g * inv_n2), u[q].y * (g * inv_n2))
+                                : make_float2(cr * sv[q] * inv_n2, 0.f);
             }
         }
         if constexpr (!ERR_ONLY) {
@@ -274,7 +294,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
             for (int t = 0; t < B; ++t) p[t] = cconjmul(twB[t * A + k], u[t]);
         }
-        __syncthreads();
+        if constexpr (kRowPerHalfWarp<N>) __syncwarp(); else __syncthreads();
 
         // Phase 7: row inverse pass 1, store y_k (lanes over t).
 #pragma unroll 1
