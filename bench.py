@@ -187,6 +187,103 @@ def run_reference(args, spec):
     return 0
 
 
+def run_batch_mode(args):
+    """16 uneven scans (N in {128, 256}, J log-uniform in [100, 2000], raster or
+    Fermat, presets cycled DC, AR, DR, SF, RAAR, RRR) advanced together through
+    one captured graph per round, against the same scans run one after another."""
+    import torch
+    from paper_2311_11466_gb300 import build as _build, native, serve, synth
+    _build.build()
+    specs = synth.batch_specs(16)
+    scans = [synth.make_scan(sp) for sp in specs]
+    names = ["DC", "AR", "DR", "SF", "RAAR", "RRR"]
+    settings = [native.PRESETS[names[i % 6]] for i in range(len(scans))]
+    n = args.steps
+    units = sum(sc.J for sc in scans) * n
+
+    def load():
+        rs = []
+        for sc in scans:
+            r = native.Reconstruction()
+            r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+            rs.append(r)
+        return rs
+
+    rs = load()
+    serve.run_batch(rs, settings, args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    serve.run_batch(rs, settings, n)
+    t_batch = time.perf_counter() - t0
+    for r in rs:
+        r.close()
+    rs = load()
+    for r, abc in zip(rs, settings):
+        r.iterate(*abc, args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, abc in zip(rs, settings):
+        r.iterate(*abc, n)
+        r.object_probe()       # synchronises this scan before the next starts
+    t_seq = time.perf_counter() - t0
+    for r in rs:
+        r.close()
+    line = {"metric": "position-updates/s, 16 uneven scans", "mode": "batch", "value": units / t_batch,
+            "unit": UNIT, "sequential": units / t_seq, "speedup": t_seq / t_batch, "steps": n,
+            "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "config": {"scans": [{"J": sc.J, "N": sc.N, "M": list(sc.M_shape),
+                                  "geometry": sc.spec.geometry} for sc in scans],
+                       "settings": [names[i % 6] for i in range(len(scans))]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_mode(args):
+    """Poisson arrivals of blind RAAR(0.9) reconstructions (N in {128, 256}, J
+    log-uniform in [100, 4096] drawn from a pool of distinct synthetic scans),
+    served with admission by HBM budget and interleaved rounds; p50/p99
+    latency and aggregate throughput, against serving the same requests one
+    after another."""
+    import numpy as np
+    from paper_2311_11466_gb300 import build as _build, native, serve, synth
+    _build.build()
+    pool_specs = synth.serving_specs(8)
+    pool = [synth.make_scan(sp) for sp in pool_specs]
+    rng = np.random.default_rng(4)
+    pick = rng.integers(0, len(pool), size=args.requests)
+    scans = [pool[i] for i in pick]
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=args.requests))
+    arrivals -= arrivals[0]
+    iters = args.e2e_iters
+    settings = [native.PRESETS["RAAR"]] * len(scans)
+    budget = 180 << 30
+    # warm the kernels once
+    serve.run_stream(scans[:1], settings[:1], 2, [0.0], budget, 1)
+    recs, wall = serve.run_stream(scans, settings, iters, arrivals, budget, max_active=16,
+                                  iters_per_round=10)
+    lat = np.array([r["latency_s"] for r in recs])
+    per100 = np.array([r["per100_s"] for r in recs])
+    units = sum(sc.J for sc in scans) * iters
+    # the same requests one at a time, back to back (no queueing model)
+    t0 = time.perf_counter()
+    for sc in scans:
+        with native.Reconstruction() as r:
+            r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+            r.iterate(*settings[0], iters)
+            r.object_probe()
+    t_seq = time.perf_counter() - t0
+    line = {"metric": "serving: aggregate position-updates/s; p50/p99 latency", "mode": "serve",
+            "value": units / wall, "unit": UNIT, "sequential": units / t_seq,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "per100_p50_s": float(np.percentile(per100, 50)), "per100_p99_s": float(np.percentile(per100, 99)),
+            "requests": len(scans), "rate_per_s": args.rate, "iterations": iters,
+            "wall_s": wall, "dtype": "f32", "data": "synthetic",
+            "config": {"pool": [{"J": sc.J, "N": sc.N} for sc in pool], "max_active": 16,
+                       "iters_per_round": 10, "budget_gb": 180}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,7 +294,14 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=20.0)
     args = ap.parse_args()
+    if args.mode == "batch":
+        return run_batch_mode(args)
+    if args.mode == "serve":
+        return run_serve_mode(args)
 
     from paper_2311_11466_gb300 import synth
     spec = synth.named_spec(args.workload)

@@ -186,13 +186,14 @@ __global__ void __launch_bounds__(kT) probe_reduce_kernel(
     if (threadIdx.x == 0) atomicMax(maxP, (unsigned long long)__double_as_longlong(bm));
 }
 
-// Probe update, plus (block 0) the iteration's Fourier error and the reset
-// of the object maximum for the next iteration.
+// Probe update, plus (block 0) the iteration's Fourier error, stored in the
+// ring at the slot of the device-side iteration counter (so a captured graph
+// replays correctly), and the reset of the object maximum.
 __global__ void __launch_bounds__(kT) probe_normalise_kernel(
     const double2* __restrict__ numP, const double* __restrict__ denP,
     const unsigned long long* __restrict__ maxP, int NN, double alpha, float2* __restrict__ P,
-    const double* __restrict__ e_part, int n_part, double inv_sumI, double* __restrict__ e_slot,
-    unsigned* __restrict__ maxO) {
+    const double* __restrict__ e_part, int n_part, double inv_sumI, double* __restrict__ e_ring,
+    unsigned long long* __restrict__ d_iter, int ring_cap, unsigned* __restrict__ maxO) {
     __shared__ double scratch[kT / 32];
     const int r = blockIdx.x * kT + threadIdx.x;
     if (r < NN) {
@@ -201,16 +202,16 @@ __global__ void __launch_bounds__(kT) probe_normalise_kernel(
         const double2 nv = numP[r];
         P[r] = d > 0.0 ? make_float2((float)(nv.x / d), (float)(nv.y / d)) : make_float2(0.f, 0.f);
     }
-    if (blockIdx.x == 0 && e_slot != nullptr) {
+    if (blockIdx.x == 0) {
         double s = 0.0;
         for (int i = threadIdx.x; i < n_part; i += kT) s += e_part[i];
         const double tot = block_sum_double<kT>(s, scratch);
         if (threadIdx.x == 0) {
-            *e_slot = tot * inv_sumI;
+            const unsigned long long k = *d_iter;
+            e_ring[k % (unsigned long long)ring_cap] = tot * inv_sumI;
+            *d_iter = k + 1;
             *maxO = 0u;
         }
-    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *maxO = 0u;
     }
 }
 
@@ -268,8 +269,9 @@ int probe_chunks(int J, int N) {
 
 cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
                           const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
-                          const double* e_part, int n_part, double inv_sumI, double* e_slot,
-                          int concur_mode, cudaStream_t st) {
+                          const double* e_part, int n_part, double inv_sumI, double* e_ring,
+                          unsigned long long* d_iter, int ring_cap, int concur_mode,
+                          cudaStream_t st) {
     const size_t M = (size_t)Mr * Mc;
     const int NN = N * N;
     if (concur_mode == 0) {
@@ -291,7 +293,8 @@ cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos
                                                           cb.numP, cb.denP, cb.maxP);
     probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cb.numP, cb.denP, cb.maxP, NN,
                                                              (double)alpha, P, e_part, n_part,
-                                                             inv_sumI, e_slot, cb.maxO);
+                                                             inv_sumI, e_ring, d_iter, ring_cap,
+                                                             cb.maxO);
     return cudaGetLastError();
 }
 

@@ -58,8 +58,9 @@ constexpr int kObjTile = 32;
 int probe_chunks(int J, int N);
 cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
                           const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
-                          const double* e_part, int n_part, double inv_sumI, double* e_slot,
-                          int concur_mode, cudaStream_t st);
+                          const double* e_part, int n_part, double inv_sumI, double* e_ring,
+                          unsigned long long* d_iter, int ring_cap, int concur_mode,
+                          cudaStream_t st);
 cudaError_t launch_form_waves(float2* x, const float2* P, const float2* O, const int2* pos,
                               int J, int N, int Mc, cudaStream_t st);
 cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, const float2* O,
@@ -67,5 +68,15 @@ cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, cons
                                cudaStream_t st);
 cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
                              cudaStream_t st);
+
+// Context internals used by the batching and serving runtime (serve.cu).
+}  // namespace ptycho
+struct ptycho_ctx;
+namespace ptycho {
+cudaStream_t ctx_stream(const ptycho_ctx* ctx);
+int ctx_device(const ptycho_ctx* ctx);
+bool ctx_loaded(const ptycho_ctx* ctx);
+// Account for iterations that ran as replays of a captured graph.
+void ctx_add_iterations(ptycho_ctx* ctx, int64_t n);
 
 }  // namespace ptycho

@@ -43,6 +43,7 @@ struct ptycho_ctx {
     float* sqrtIp = nullptr;
     int2* pos = nullptr;
     double *e_part = nullptr, *e_ring = nullptr, *e_tmp = nullptr;
+    unsigned long long* d_iter = nullptr;  // device-side iteration counter (ring slot)
     int* dflag = nullptr;
     ConcurBufs cb{};
     std::vector<void*> allocs;
@@ -106,6 +107,7 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->sqrtIp = nullptr;
     ctx->pos = nullptr;
     ctx->e_part = ctx->e_ring = ctx->e_tmp = nullptr;
+    ctx->d_iter = nullptr;
     ctx->dflag = nullptr;
     ctx->cb = ConcurBufs{};
     ctx->loaded = false;
@@ -140,6 +142,13 @@ int materialise(ptycho_ctx* ctx) {
 }
 
 }  // namespace
+
+namespace ptycho {
+cudaStream_t ctx_stream(const ptycho_ctx* ctx) { return ctx->stream; }
+int ctx_device(const ptycho_ctx* ctx) { return ctx->opts.device; }
+bool ctx_loaded(const ptycho_ctx* ctx) { return ctx->loaded; }
+void ctx_add_iterations(ptycho_ctx* ctx, int64_t n) { ctx->iters += n; }
+}  // namespace ptycho
 
 extern "C" {
 
@@ -315,6 +324,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->e_part, (size_t)J * C);
     PT_ALLOC(ctx->e_ring, (size_t)kRing);
     PT_ALLOC(ctx->e_tmp, (size_t)4);
+    PT_ALLOC(ctx->d_iter, (size_t)1);
     PT_ALLOC(ctx->dflag, (size_t)4);
     PT_ALLOC(ctx->cb.numO, M);
     PT_ALLOC(ctx->cb.denO, M);
@@ -362,6 +372,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
         PT_STEP(cudaMemcpyAsync(ctx->cb.tile_list, tile_list.data(), tile_list.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, st));
     PT_STEP(cudaMemsetAsync(ctx->dflag, 0, 4 * sizeof(int), st));
+    PT_STEP(cudaMemsetAsync(ctx->d_iter, 0, sizeof(unsigned long long), st));
     PT_STEP(cudaMemsetAsync(ctx->cb.maxO, 0, sizeof(unsigned), st));
     PT_STEP(cudaMemsetAsync(ctx->cb.maxP, 0, sizeof(unsigned long long), st));
     // The intensities pass through the y buffer (twice their size) on their way
@@ -425,10 +436,10 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
         PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 1], ctx->stream));
-        double* slot = ctx->e_ring + (ctx->iters % kRing);
         PT_CUDA(ctx, launch_concur(ctx->y, ctx->P, ctx->O, ctx->pos, ctx->cb, ctx->J, ctx->N,
                                    ctx->Mr, ctx->Mc, ctx->opts.alpha, ctx->e_part,
-                                   ctx->J * ctx->C, inv_sumI, slot, ctx->opts.concur, ctx->stream));
+                                   ctx->J * ctx->C, inv_sumI, ctx->e_ring, ctx->d_iter, kRing,
+                                   ctx->opts.concur, ctx->stream));
         if (rec) {
             PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 2], ctx->stream));
             ctx->prof_n++;
