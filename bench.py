@@ -105,6 +105,16 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        # a kernel timed inside a long step: the sustained figure
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured (sustained)"
+    return 1700.0, "fallback (sustained)"
+
+
 def _kernel_hash() -> str:
     h = hashlib.sha256()
     for f in ("divide.cu", "common.cuh"):
@@ -295,6 +305,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rate", type=float, default=20.0)
     args = ap.parse_args()
@@ -304,6 +315,8 @@ def main():
         return run_serve_mode(args)
 
     from paper_2311_11466_gb300 import synth
+    if args.precision == "bf16x3" and args.workload == "large":
+        args.workload = "precision"
     spec = synth.named_spec(args.workload)
     if args.impl == "reference":
         return run_reference(args, spec)
@@ -326,7 +339,7 @@ def main():
     J, N = scan.J, scan.N
     # one dedicated stream for the library and for the timing events
     stream = torch.cuda.Stream(device=local)
-    r = native.Reconstruction(device=local, stream=stream.cuda_stream)
+    r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
     r.iterate(*RAAR, args.warmup)
     torch.cuda.synchronize()
@@ -364,6 +377,20 @@ def main():
     hbm, peak_kind = _peaks()
     achieved = div_bytes / div_avg / 1e9
     traffic = _profiled_traffic()
+    if args.precision == "bf16x3":
+        flops = 96.0 * N ** 3 * J   # four GEMMs of 2 x N x 2N x 6N per exit wave
+        tflops, tkind = _bf16_peak()
+        roof = {"bound": "tensor", "achieved": flops / div_avg / 1e12, "peak": tflops,
+                "unit": "TFLOP/s", "frac": flops / div_avg / 1e12 / tflops, "traffic": None,
+                "kernel": "divide on tensor cores (prologue + 4 BF16x3 DFT GEMMs, tcgen05)",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": div_avg * 1e3,
+                "peak_source": tkind}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": "divide (fused re-split + FFT + modulus + IFFT)",
+                "algorithmic_bytes_per_launch": div_bytes,
+                "avg_launch_ms": div_avg * 1e3, "peak_source": peak_kind}
 
     # end to end through the public API with host buffers (pinned)
     def pin(a):
@@ -377,7 +404,7 @@ def main():
     if ws > 1:
         dist.barrier()
     w0 = time.perf_counter()
-    re2e = native.Reconstruction(device=local, stream=stream.cuda_stream)
+    re2e = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
     re2e.load_scan(pos_h, I_h, O_h, P_h)
     re2e.iterate(*RAAR, e2e_iters)
     native.ptycho_get_object_probe(re2e.h, O_out, P_out)
@@ -410,20 +437,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16x3 (f32 accumulate)", "data": "synthetic",
             "config": {"workload": f"{args.workload}: J={J}, N={N}, M={scan.M_shape[0]}x{scan.M_shape[1]}, "
-                                   f"RAAR(0.9) (a,b,c)=(0.5,1.8,2.0), FP32, Poisson {spec.photons}",
+                                   f"RAAR(0.9) (a,b,c)=(0.5,1.8,2.0), {args.precision}, Poisson {spec.photons}",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "working set 1.3 GB > L2 (no flush needed)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "divide (fused re-split + FFT + modulus + IFFT)",
-                         "algorithmic_bytes_per_launch": div_bytes,
-                         "avg_launch_ms": div_avg * 1e3, "peak_source": peak_kind},
+            "roofline": roof,
             "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
             "per_step_bytes": 52.0 * J * NN,
             "step_hbm_gbs": 52.0 * J * NN / (ms / args.steps / 1e3) / 1e9,
-            "gpu_launches": KERNELS_PER_ITER * args.steps,
+            "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)) * args.steps,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

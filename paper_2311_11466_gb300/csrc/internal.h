@@ -69,6 +69,18 @@ cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, cons
 cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
                              cudaStream_t st);
 
+// Tensor-core (BF16 x 3) divide path (dft_gemm.cu).
+bool bf16x3_supported(int N);
+int bf16x3_tiles(int N, int J);
+void bf16x3_constants(int N, std::vector<uint16_t>& fwd_hi, std::vector<uint16_t>& fwd_lo,
+                      std::vector<uint16_t>& inv_hi, std::vector<uint16_t>& inv_lo);
+cudaError_t bf16x3_prepare();
+cudaError_t launch_sqrt_transpose(int N, const float* I, float* out, double* psum, int* bad, int J,
+                                  cudaStream_t st);
+cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt,
+                                 uint16_t* const planes[4], const uint16_t* const B[4],
+                                 int* err_flag, cudaStream_t st);
+
 // Context internals used by the batching and serving runtime (serve.cu).
 }  // namespace ptycho
 struct ptycho_ctx;

@@ -41,6 +41,11 @@ struct ptycho_ctx {
 
     float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
     float* sqrtIp = nullptr;
+    // tensor-core path: sqrt(I) transposed, two ping-pong operand buffers (hi,
+    // lo) and the constant DFT operands (fwd hi, fwd lo, inv hi, inv lo)
+    float* sqrtIt = nullptr;
+    uint16_t* planes[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint16_t* Bc[4] = {nullptr, nullptr, nullptr, nullptr};
     int2* pos = nullptr;
     double *e_part = nullptr, *e_ring = nullptr, *e_tmp = nullptr;
     unsigned long long* d_iter = nullptr;  // device-side iteration counter (ring slot)
@@ -105,6 +110,8 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->bytes = 0;
     ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;
     ctx->sqrtIp = nullptr;
+    ctx->sqrtIt = nullptr;
+    for (int i = 0; i < 4; ++i) ctx->planes[i] = ctx->Bc[i] = nullptr;
     ctx->pos = nullptr;
     ctx->e_part = ctx->e_ring = ctx->e_tmp = nullptr;
     ctx->d_iter = nullptr;
@@ -132,6 +139,19 @@ struct DeviceGuard {
         if (prev >= 0 && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// After a synchronisation: a bounded device wait of the tensor-core kernels
+// that expired leaves a flag; report it once.
+int check_device_flags(ptycho_ctx* ctx) {
+    if (ctx->opts.precision != PTYCHO_PREC_BF16X3 || !ctx->dflag) return PTYCHO_OK;
+    int f = 0;
+    PT_CUDA(ctx, cudaMemcpy(&f, ctx->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        PT_CUDA(ctx, cudaMemset(ctx->dflag + 1, 0, sizeof(int)));
+        return fail(ctx, PTYCHO_ETIMEOUT, "a bounded wait in the tensor-core DFT kernel expired");
+    }
+    return PTYCHO_OK;
+}
 
 int materialise(ptycho_ctx* ctx) {
     if (ctx->have_x) return PTYCHO_OK;
@@ -191,10 +211,6 @@ int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts) {
                          (e != cudaSuccess ? cudaGetErrorString(e) : std::to_string(o.device));
         return e != cudaSuccess ? PTYCHO_ECUDA : PTYCHO_EINVAL;
     }
-    if (o.precision == PTYCHO_PREC_BF16X3) {
-        g_create_error = "BF16X3 precision is not available in this build";
-        return PTYCHO_EINVAL;
-    }
     DeviceGuard dg(o.device);
     ptycho_ctx* ctx = new ptycho_ctx();
     ctx->opts = o;
@@ -231,7 +247,6 @@ const char* ptycho_last_error(const ptycho_ctx* ctx) {
 }
 
 size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, int precision) {
-    (void)precision;
     if (J <= 0 || N <= 0 || M_rows <= 0 || M_cols <= 0) return 0;
     const size_t NN = (size_t)N * N, M = (size_t)M_rows * M_cols;
     const int C = divide_cluster_size(N) > 0 ? divide_cluster_size(N) : 1;
@@ -249,6 +264,14 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += NN * (sizeof(double2) + sizeof(double));
     b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
+    if (precision == PTYCHO_PREC_BF16X3) {
+        b += (size_t)J * NN * sizeof(float);           // sqrt(I) transposed
+        b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
+        b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
+        b += (size_t)J * (NN / 1024 + 1) * sizeof(double);
+        const size_t tiles = (size_t)J * (N / 128 > 0 ? (N / 128) * (N / 128) : 1);
+        if (tiles > (size_t)J * C) b += (tiles - (size_t)J * C) * sizeof(double);
+    }
     return b;
 }
 
@@ -261,6 +284,9 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     if (!divide_supported(N))
         return fail(ctx, PTYCHO_EINVAL, "N must be one of 8, 16, 32, 64, 128, 256");
     if (M_rows < N || M_cols < N) return fail(ctx, PTYCHO_EINVAL, "object smaller than the probe");
+    const bool tc = ctx->opts.precision == PTYCHO_PREC_BF16X3;
+    if (tc && !bf16x3_supported(N))
+        return fail(ctx, PTYCHO_EINVAL, "BF16X3 precision needs N = 128 or 256");
     if (!pos_rc || !intensity || !obj0 || !probe0)
         return fail(ctx, PTYCHO_EINVAL, "NULL input pointer");
     if ((size_t)J * N * N > (size_t)1 << 40) return fail(ctx, PTYCHO_EINVAL, "scan too large");
@@ -337,6 +363,19 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
     PT_ALLOC(ctx->cb.tile_list, tile_list.size() > 0 ? tile_list.size() : 1);
     PT_ALLOC(psum, (size_t)J * sq_blocks);
+    double* psum_t = nullptr;
+    if (tc) {
+        PT_ALLOC(ctx->sqrtIt, (size_t)J * NN);
+        for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
+        for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->Bc[i], 4 * NN);
+        PT_ALLOC(psum_t, (size_t)J * (NN / 1024));
+        const int tiles = bf16x3_tiles(N, J);
+        if (tiles > J * C) {
+            double* more = nullptr;
+            PT_ALLOC(more, (size_t)tiles);
+            ctx->e_part = more;  // the larger buffer serves both paths
+        }
+    }
 #undef PT_ALLOC
     ctx->cb.tiles_r = tiles_r;
     ctx->cb.tiles_c = tiles_c;
@@ -384,6 +423,16 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
         Idev = reinterpret_cast<const float*>(ctx->y);
     }
     PT_STEP(launch_sqrt_permute(N, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
+    if (tc) {
+        PT_STEP(bf16x3_prepare());
+        PT_STEP(launch_sqrt_transpose(N, Idev, ctx->sqrtIt, psum_t, ctx->dflag, J, st));
+        std::vector<uint16_t> Bh[4];
+        bf16x3_constants(N, Bh[0], Bh[1], Bh[2], Bh[3]);
+        for (int i = 0; i < 4; ++i)
+            PT_STEP(cudaMemcpyAsync(ctx->Bc[i], Bh[i].data(), Bh[i].size() * sizeof(uint16_t),
+                                    cudaMemcpyHostToDevice, st));
+        PT_STEP(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    }
     PT_STEP(launch_form_waves(ctx->x, ctx->P, ctx->O, ctx->pos, J, N, M_cols, st));
     std::vector<double> hsum((size_t)J * sq_blocks);
     int bad = 0;
@@ -434,11 +483,18 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         da.err_only = 0;
         const bool rec = ctx->prof && ctx->prof_n < kProfMax;
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
-        PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+        int n_part = ctx->J * ctx->C;
+        if (ctx->opts.precision == PTYCHO_PREC_BF16X3) {
+            PT_CUDA(ctx, launch_divide_bf16x3(da, ctx->N, ctx->sqrtIt, ctx->planes, ctx->Bc,
+                                              ctx->dflag + 1, ctx->stream));
+            n_part = bf16x3_tiles(ctx->N, ctx->J);
+        } else {
+            PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+        }
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 1], ctx->stream));
         PT_CUDA(ctx, launch_concur(ctx->y, ctx->P, ctx->O, ctx->pos, ctx->cb, ctx->J, ctx->N,
                                    ctx->Mr, ctx->Mc, ctx->opts.alpha, ctx->e_part,
-                                   ctx->J * ctx->C, inv_sumI, ctx->e_ring, ctx->d_iter, kRing,
+                                   n_part, inv_sumI, ctx->e_ring, ctx->d_iter, kRing,
                                    ctx->opts.concur, ctx->stream));
         if (rec) {
             PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 2], ctx->stream));
@@ -464,7 +520,7 @@ int ptycho_get_object_probe(ptycho_ctx* ctx, float* obj_out, float* probe_out) {
         PT_CUDA(ctx, cudaMemcpyAsync(probe_out, ctx->P, (size_t)ctx->N * ctx->N * sizeof(float2),
                                      cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return PTYCHO_OK;
+    return check_device_flags(ctx);
 }
 
 int ptycho_set_object_probe(ptycho_ctx* ctx, const float* obj, const float* probe) {
@@ -496,7 +552,7 @@ int ptycho_get_exit_waves(ptycho_ctx* ctx, float* x_out) {
     PT_CUDA(ctx, cudaMemcpyAsync(x_out, ctx->x, (size_t)ctx->J * ctx->N * ctx->N * sizeof(float2),
                                  cudaMemcpyDeviceToHost, ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return PTYCHO_OK;
+    return check_device_flags(ctx);
 }
 
 int ptycho_set_exit_waves(ptycho_ctx* ctx, const float* x) {
@@ -532,7 +588,7 @@ int ptycho_errors(ptycho_ctx* ctx, double* fourier_err, int32_t cap, int32_t* n_
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (int32_t i = 0; i < n; ++i) fourier_err[i] = ring[(size_t)((first + i) % kRing)];
     *n_written = n;
-    return PTYCHO_OK;
+    return check_device_flags(ctx);
 }
 
 int64_t ptycho_iteration_count(const ptycho_ctx* ctx) { return ctx && ctx->loaded ? ctx->iters : 0; }
