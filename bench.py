@@ -48,6 +48,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks of the default process group (or value)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job rate of independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -306,6 +322,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--preset", default="RAAR", choices=["DC", "AR", "DR", "SF", "RAAR", "RRR"])
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rate", type=float, default=20.0)
     args = ap.parse_args()
@@ -341,7 +358,8 @@ def main():
     stream = torch.cuda.Stream(device=local)
     r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
-    r.iterate(*RAAR, args.warmup)
+    abc = native.PRESETS[args.preset]
+    r.iterate(*abc, args.warmup)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -354,7 +372,7 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    r.iterate(*RAAR, args.steps)
+    r.iterate(*abc, args.steps)
     t1.record(stream)
     t1.synchronize()
     if ws > 1:
@@ -364,15 +382,16 @@ def main():
     clocks = sampler.stop() if rank == 0 else None
     native.ptycho_profile_enable(r.h, False)
     div_ms, con_ms, nrec = native.ptycho_profile_read(r.h)
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ws * J * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, torch.device("cuda", local))
+    value = replica_throughput(J * args.steps, ws, ms / 1e3)
 
     # roofline of the dominant kernel (the divide kernel)
     NN = N * N
-    div_bytes = 36.0 * J * NN   # x, y (8 + 8 read), sqrt I (4), x, y (8 + 8 written)
+    # algorithmic bytes per pixel of the divide kernel: sqrt I (4) and y_k (8)
+    # always; y_{k-1} (8) when b != 1; x_{k-1} read and x_k written (8 + 8) when a != 1
+    a_, b_, _ = abc
+    div_px = 12.0 + (8.0 if b_ != 1.0 else 0.0) + (16.0 if a_ != 1.0 else 0.0)
+    div_bytes = div_px * J * NN
     div_avg = div_ms / max(nrec, 1) / 1e3
     hbm, peak_kind = _peaks()
     achieved = div_bytes / div_avg / 1e9
@@ -406,20 +425,17 @@ def main():
     w0 = time.perf_counter()
     re2e = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
     re2e.load_scan(pos_h, I_h, O_h, P_h)
-    re2e.iterate(*RAAR, e2e_iters)
+    re2e.iterate(*abc, e2e_iters)
     native.ptycho_get_object_probe(re2e.h, O_out, P_out)
     errs = re2e.errors()
     w1 = time.perf_counter()
     e2e_s = w1 - w0
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, torch.device("cuda", local))
     final_model_err = re2e.model_error()
     re2e.close()
     h2d = I_h.nbytes + pos_h.nbytes + O_h.nbytes + P_h.nbytes
     d2h = O_out.nbytes + P_out.nbytes + errs.nbytes
-    e2e = {"value": ws * J * e2e_iters / e2e_s, "unit": UNIT,
+    e2e = {"value": replica_throughput(J * e2e_iters, ws, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": h2d / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
            "step": f"one reconstruction = load_scan (host, pinned) + {e2e_iters} RAAR iterations "
                    f"+ object/probe/error read-back; bytes per iteration",
@@ -440,13 +456,13 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "bf16x3 (f32 accumulate)", "data": "synthetic",
             "config": {"workload": f"{args.workload}: J={J}, N={N}, M={scan.M_shape[0]}x{scan.M_shape[1]}, "
-                                   f"RAAR(0.9) (a,b,c)=(0.5,1.8,2.0), {args.precision}, Poisson {spec.photons}",
+                                   f"{args.preset} (a,b,c)={tuple(abc)}, {args.precision}, Poisson {spec.photons}",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "working set 1.3 GB > L2 (no flush needed)"},
             "roofline": roof,
             "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
-            "per_step_bytes": 52.0 * J * NN,
-            "step_hbm_gbs": 52.0 * J * NN / (ms / args.steps / 1e3) / 1e9,
+            "per_step_bytes": (div_px + 16.0) * J * NN,
+            "step_hbm_gbs": (div_px + 16.0) * J * NN / (ms / args.steps / 1e3) / 1e9,
             "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)) * args.steps,
             "clocks": clocks,
             "e2e": e2e,
