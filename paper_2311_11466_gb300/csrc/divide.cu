@@ -6,24 +6,27 @@
 //   y_k  = F^{-1}( c sqrt(I_j) Psi/|Psi| + (1 - c) Psi )
 //   e_j  = sum_q (|Psi| - sqrt(I_j))^2
 //
-// One thread-block cluster of C CTAs owns one N x N exit wave; CTA c holds
-// R = N / C consecutive rows in shared memory (FP32 complex).  Every 1-D DFT
-// of length N = A * B runs as two in-register passes in place in shared
-// memory: pass 1 takes the A elements t + B e (e < A) of one thread, a DFT of
-// length A and the twiddle W_N^{t k}; pass 2 takes the B elements of one k, a
-// DFT of length B.  The spectrum is left in that digit-permuted order (the
-// sqrt(I) array is stored in the same order at load time).
+// One thread-block cluster of C CTAs works on one N x N exit wave at a time;
+// CTA c holds R = N / C rows in shared memory (FP32 complex).  Every 1-D DFT
+// of length N = A * B runs as two in-register passes: pass 1 takes the A
+// elements t + B e (e < A) of one thread, a DFT of length A and the twiddle
+// W_N^{t k}; pass 2 takes the B elements of one k, a DFT of length B.  The
+// spectrum is left in that digit-permuted order (sqrt(I) is stored in the
+// same order at load time).
 //
-// The row DFT's second pass pushes its outputs straight into the CTA that
-// owns their column frequencies (distributed shared memory stores), so the
-// transpose costs no pass of its own; the inverse column pass pushes back the
-// same way.  Each push is bracketed by two cluster barriers: all CTAs finish
-// reading the slots about to be overwritten, then all pushes land before the
-// next pass reads them.  Four cluster barriers per exit wave.
+// The two transposes of the 2-D DFT (row pass -> column pass and back) go
+// through a small scratch area in global memory, one slot of 2 N^2 complex
+// per cluster: the row pass's second half stores its outputs there in the
+// column-major order the other CTAs need, one cluster barrier (release /
+// acquire, cluster scope) later the column pass reads them straight into
+// registers (L2-cached loads); the inverse goes back the same way.  Clusters
+// are persistent (as many as fit on the GPU at once, each looping over exit
+// waves), so every cluster keeps reusing its own slot and the scratch stays
+// resident in L2.  Two cluster barriers per exit wave.
 //
 // Shared-memory row layout: element t + B e of a row lives at slot e (B + 1) + t
-// so both passes read conflict-free; the row stride RS makes the passes whose
-// lanes run over rows conflict-free as well.
+// so both passes are bank-conflict free; the row stride RS keeps the passes
+// whose lanes run over rows conflict free as well.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -36,9 +39,9 @@ namespace cg = cooperative_groups;
 namespace ptycho {
 namespace {
 
-template <int N> struct Cfg;
 // A x B radix split, cluster size C, threads T, row stride residue RSM (mod
 // 16), and the CTAs per SM the register budget is sized for (MINB).
+template <int N> struct Cfg;
 template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 32,  RSM = 9, MINB = 4; };
 template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64,  RSM = 9, MINB = 4; };
 template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
@@ -50,11 +53,10 @@ template <int N>
 struct Geo {
     static constexpr int A = Cfg<N>::A, B = Cfg<N>::B, C = Cfg<N>::C, T = Cfg<N>::T;
     static constexpr int R = N / C;       // rows per CTA
-    static constexpr int KC = A / C;      // pass-2 indices k owned per CTA after the transpose
+    static constexpr int KC = A / C;      // pass-2 indices k per CTA
     static constexpr int RS0 = A * (B + 1);
     static constexpr int RS = RS0 + ((Cfg<N>::RSM - RS0 % 16) + 16) % 16;  // row stride
     static constexpr int TP2 = (R * A + T - 1) / T;  // pass-2 tasks per thread
-    static constexpr int TP5 = (R * B + T - 1) / T;  // inverse column pass-1 tasks per thread
     static constexpr size_t SMEM = (size_t)R * RS * sizeof(float2) + 2 * N * sizeof(float2) +
                                    32 * sizeof(double);
     static_assert(A * B == N, "radix split");
@@ -66,19 +68,6 @@ struct Geo {
 template <int N>
 constexpr bool kRowPerHalfWarp = Geo<N>::A == 16 && Geo<N>::B == 16 && Geo<N>::R * 16 == Geo<N>::T;
 
-// Slot of the spectral index q of CTA cta (pass-2 index k = cta KC + q / B, output q % B).
-template <int N>
-__device__ __forceinline__ int slot_freq(int cta, int q) {
-    using G = Geo<N>;
-    return (cta * G::KC + q / G::B) * (G::B + 1) + q % G::B;
-}
-// Slot of spatial index r = t + B e.
-template <int N>
-__device__ __forceinline__ int slot_space(int r) {
-    using G = Geo<N>;
-    return (r / G::B) * (G::B + 1) + r % G::B;
-}
-
 // One bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
 // multiple of 16); it does not wait and brings nothing into the SM.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
@@ -88,41 +77,47 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 template <int N, bool ERR_ONLY>
 __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const DivideArgs args) {
     using G = Geo<N>;
-    constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS, KC = G::KC;
-    constexpr int TP2 = G::TP2, TP5 = G::TP5;
+    constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS;
+    constexpr int TP2 = G::TP2;
+    constexpr size_t NN = (size_t)N * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* twA = buf + R * RS;   // twA[k B + t] = W_N^{t k}
     float2* twB = twA + N;        // twB[t A + k] = W_N^{t k}
-    double* red = reinterpret_cast<double*>(twB + N);
+    float* redf = reinterpret_cast<float*>(twB + N);
 
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
-    const int j = blockIdx.x / C;
     const int tid = threadIdx.x;
-
-    // Start streaming this CTA's rows of x, y and sqrt(I) into L2 at once, so
-    // the scattered per-thread loads below meet lines already on their way.
-    if (tid == 0) {
-        const size_t off = (size_t)j * N * N + (size_t)c * R * N;
-        constexpr unsigned cbytes = (unsigned)(R * N * sizeof(float2));
-        if (args.load_x || args.pa != 1.0f) prefetch_l2(args.x + off, cbytes);
-        if (!args.load_x && args.pb != 1.0f) prefetch_l2(args.y + off, cbytes);
-        prefetch_l2(args.sqrtIp + off, (unsigned)(R * N * sizeof(float)));
-    }
+    const int slot = (int)(blockIdx.x / C);
+    const int n_clusters = (int)(gridDim.x / C);
+    // the cluster's scratch: S[v'][r] (row pass -> column pass), S2[r][v'] (back)
+    float2* S = args.scratch + (size_t)slot * 2 * NN;
+    float2* S2 = S + NN;
 
     for (int i = tid; i < N; i += T) {
         const float2 w = args.tw[i];
         twA[i] = w;
         twB[(i % B) * A + i / B] = w;
     }
-    __syncthreads();
 
-    const int2 s = args.pos[j];
-    const size_t pat = (size_t)j * N * N;
-    const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
     const bool load_x = args.load_x != 0, write_x = args.write_x != 0;
     const bool need_y = args.pb != 1.0f, need_xp = args.pa != 1.0f;
+
+#pragma unroll 1
+    for (int j = slot; j < args.J; j += n_clusters) {
+    const size_t pat = (size_t)j * NN;
+    if (tid == 0) {
+        // stream this CTA's rows of x, y and sqrt(I) into L2 at once
+        const size_t off = pat + (size_t)c * R * N;
+        constexpr unsigned cbytes = (unsigned)(R * N * sizeof(float2));
+        if (load_x || need_xp) prefetch_l2(args.x + off, cbytes);
+        if (!load_x && need_y) prefetch_l2(args.y + off, cbytes);
+        prefetch_l2(args.sqrtIp + off, (unsigned)(R * N * sizeof(float)));
+    }
+    __syncthreads();  // twiddles loaded / the previous wave's shared-memory reads done
+    const int2 s = args.pos[j];
+    const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
 
     // Phase 1: form x_k, row DFT pass 1 (lanes over t).
 #pragma unroll 1
@@ -152,46 +147,36 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     }
     __syncthreads();
 
-    // Phase 2: row DFT pass 2 (lanes over rows), pushed transposed to the CTA
-    // owning each column frequency.
-    {
-        float2 u[TP2][B];
+    // Phase 2: row DFT pass 2 (lanes over rows); column frequency v' = k B + q
+    // of spatial row r goes to S[v'][r].
 #pragma unroll
-        for (int i = 0; i < TP2; ++i) {
-            const int task = tid + i * T;
-            if (task < R * A) {
-                const int k = task / R, row = task % R;
-                const float2* p = buf + row * RS + k * (B + 1);
+    for (int i = 0; i < TP2; ++i) {
+        const int task = tid + i * T;
+        if (task < R * A) {
+            const int k = task / R, row = task % R;
+            const float2* p = buf + row * RS + k * (B + 1);
+            float2 u[B];
 #pragma unroll
-                for (int t = 0; t < B; ++t) u[i][t] = p[t];
-            }
+            for (int t = 0; t < B; ++t) u[t] = p[t];
+            dft_reg<B, false>(u);
+            float2* dst = S + (size_t)(k * B) * N + c * R + row;
+#pragma unroll
+            for (int q = 0; q < B; ++q) dst[(size_t)q * N] = u[q];
         }
-        cl.sync();
-#pragma unroll
-        for (int i = 0; i < TP2; ++i) {
-            const int task = tid + i * T;
-            if (task < R * A) {
-                const int k = task / R, row = task % R;
-                dft_reg<B, false>(u[i]);
-                const int owner = k / KC;
-                float2* dst = cl.map_shared_rank(buf, owner) +
-                              ((k - owner * KC) * B) * RS + slot_space<N>(c * R + row);
-#pragma unroll
-                for (int q = 0; q < B; ++q) dst[q * RS] = u[i][q];
-            }
-        }
-        cl.sync();
     }
+    cl.sync();  // every CTA's rows are in S (release / acquire, cluster scope)
 
-    // Phase 3: column DFT pass 1 (rows now hold whole columns; lanes over t).
+    // Phase 3: column DFT pass 1 over this CTA's column frequencies
+    // v' = c R + rho (lanes over t), read from S.
 #pragma unroll 1
     for (int task = tid; task < R * B; task += T) {
-        const int row = task / B, t = task % B;
-        float2* p = buf + row * RS + t;
+        const int rho = task / B, t = task % B;
+        const float2* src = S + (size_t)(c * R + rho) * N + t;
         float2 v[A];
 #pragma unroll
-        for (int e = 0; e < A; ++e) v[e] = p[e * (B + 1)];
+        for (int e = 0; e < A; ++e) v[e] = __ldcg(src + B * e);
         dft_reg<A, false>(v);
+        float2* p = buf + rho * RS + t;
 #pragma unroll
         for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], twA[k * B + t]);
     }
@@ -249,48 +234,42 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 
     if constexpr (!ERR_ONLY) {
         __syncthreads();
-        // Phase 5: column inverse pass 1 (lanes over the local rows), pushed
-        // back to the CTA owning each spatial row.
-        {
-            float2 v[TP5][A];
+        // Phase 5: column inverse pass 1 (lanes over the local rows rho);
+        // spatial row r = t + B e of column frequency v' goes to S2[r][v'].
+#pragma unroll 1
+        for (int task = tid; task < R * B; task += T) {
+            const int t = task / R, rho = task % R;
+            const float2* p = buf + rho * RS + t;
+            float2 v[A];
 #pragma unroll
-            for (int i = 0; i < TP5; ++i) {
-                const int task = tid + i * T;
-                if (task < R * B) {
-                    const int t = task / R, rho = task % R;
-                    const float2* p = buf + rho * RS + t;
+            for (int k = 0; k < A; ++k) v[k] = p[k * (B + 1)];
+            dft_reg<A, true>(v);
+            float2* dst = S2 + (size_t)t * N + c * R + rho;
 #pragma unroll
-                    for (int k = 0; k < A; ++k) v[i][k] = p[k * (B + 1)];
-                }
-            }
-            cl.sync();
-#pragma unroll
-            for (int i = 0; i < TP5; ++i) {
-                const int task = tid + i * T;
-                if (task < R * B) {
-                    const int t = task / R, rho = task % R;
-                    dft_reg<A, true>(v[i]);
-                    const int sf = slot_freq<N>(c, rho);
-#pragma unroll
-                    for (int e = 0; e < A; ++e) {
-                        const int r = t + B * e;
-                        float2* dst = cl.map_shared_rank(buf, r / R);
-                        dst[(r % R) * RS + sf] = v[i][e];
-                    }
-                }
-            }
-            cl.sync();
+            for (int e = 0; e < A; ++e) dst[(size_t)(B * e) * N] = v[e];
         }
+        cl.sync();  // every CTA's columns are in S2
 
-        // Phase 6: row inverse pass 2 with the conjugate twiddle (lanes over k).
+        // Phase 6: row inverse pass 2 with the conjugate twiddle (lanes over k),
+        // this CTA's rows read from S2.
 #pragma unroll 1
         for (int task = tid; task < R * A; task += T) {
             const int row = task / A, k = task % A;
-            float2* p = buf + row * RS + k * (B + 1);
+            const float2* src = S2 + (size_t)(c * R + row) * N + k * B;
             float2 u[B];
+            if constexpr (B % 2 == 0) {
 #pragma unroll
-            for (int t = 0; t < B; ++t) u[t] = p[t];
+                for (int t = 0; t < B; t += 2) {
+                    const float4 f = __ldcg(reinterpret_cast<const float4*>(src + t));
+                    u[t] = make_float2(f.x, f.y);
+                    u[t + 1] = make_float2(f.z, f.w);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < B; ++t) u[t] = __ldcg(src + t);
+            }
             dft_reg<B, true>(u);
+            float2* p = buf + row * RS + k * (B + 1);
 #pragma unroll
             for (int t = 0; t < B; ++t) p[t] = cconjmul(twB[t * A + k], u[t]);
         }
@@ -312,8 +291,22 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         }
     }
 
-    const double tot = block_sum_double<T>((double)err, red);
-    if (tid == 0) args.e_part[(size_t)j * C + c] = tot;
+    // CTA partial in FP32 (FP64 is slow on this part); the sum over all CTAs
+    // is taken in FP64 by the concur step
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) err += __shfl_down_sync(0xffffffffu, err, o);
+    if ((tid & 31) == 0) redf[tid >> 5] = err;
+    __syncthreads();
+    if (tid == 0) {
+        float tot = 0.f;
+#pragma unroll
+        for (int w = 0; w < T / 32; ++w) tot += redf[w];
+        args.e_part[(size_t)j * C + c] = (double)tot;
+    }
+    // without the inverse half (error only), the next wave's row pass must not
+    // overwrite S before every CTA has read it
+    if constexpr (ERR_ONLY) cl.sync();
+    }  // exit waves
 }
 
 template <int N>
@@ -360,7 +353,8 @@ template <int N>
 cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     using G = Geo<N>;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)a.J * G::C);
+    const int clusters = a.J < a.n_slots ? a.J : a.n_slots;
+    cfg.gridDim = dim3((unsigned)clusters * G::C);
     cfg.blockDim = dim3(G::T);
     cfg.dynamicSmemBytes = G::SMEM;
     cfg.stream = st;
@@ -432,6 +426,40 @@ cudaError_t divide_prepare(int N) {
         case 256: return prepare_t<256>();
     }
     return cudaErrorInvalidValue;
+}
+
+template <int N>
+int slots_t() {
+    using G = Geo<N>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G::C * 1024);
+    cfg.blockDim = dim3(G::T);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, divide_kernel<N, false>, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 0;
+    }
+    return n;
+}
+
+int divide_slots(int N) {
+    switch (N) {
+        case 8: return slots_t<8>();
+        case 16: return slots_t<16>();
+        case 32: return slots_t<32>();
+        case 64: return slots_t<64>();
+        case 128: return slots_t<128>();
+        case 256: return slots_t<256>();
+    }
+    return 0;
 }
 
 cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st) {

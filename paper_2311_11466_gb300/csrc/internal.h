@@ -25,6 +25,8 @@ struct DivideArgs {
     float c;              // divide relaxation
     int write_x;          // store x_k to x[] (needed when this iteration's a != 1)
     int err_only;         // only the Fourier error of x_k (no y written)
+    float2* scratch;      // [n_slots][2 N^2] transpose scratch, one slot per resident cluster
+    int n_slots;
 };
 
 // Supported pattern sides.
@@ -33,6 +35,9 @@ int divide_cluster_size(int N);
 // Twiddle table of the divide kernel for side N (host, FP64 rounded to FP32).
 void divide_twiddles(int N, std::vector<float2>& tw);
 cudaError_t divide_prepare(int N);  // one-time kernel attributes
+// Clusters of the divide kernel that fit on the device at once (after
+// divide_prepare); the kernel runs that many persistent clusters.
+int divide_slots(int N);
 cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st);
 // sqrt of the intensities into the divide kernel's frequency order; flags
 // *bad (device int) if any value is negative or not finite; per-pattern sums

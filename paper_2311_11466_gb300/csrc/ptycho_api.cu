@@ -41,6 +41,8 @@ struct ptycho_ctx {
 
     float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
     float* sqrtIp = nullptr;
+    float2* scratch = nullptr;  // divide-kernel transpose slots, one per resident cluster
+    int n_slots = 0;
     // tensor-core path: sqrt(I) transposed, two ping-pong operand buffers (hi,
     // lo) and the constant DFT operands (fwd hi, fwd lo, inv hi, inv lo)
     float* sqrtIt = nullptr;
@@ -110,6 +112,8 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->bytes = 0;
     ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;
     ctx->sqrtIp = nullptr;
+    ctx->scratch = nullptr;
+    ctx->n_slots = 0;
     ctx->sqrtIt = nullptr;
     for (int i = 0; i < 4; ++i) ctx->planes[i] = ctx->Bc[i] = nullptr;
     ctx->pos = nullptr;
@@ -264,6 +268,12 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += NN * (sizeof(double2) + sizeof(double));
     b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
+    {
+        int slots = divide_supported(N) && divide_prepare(N) == cudaSuccess ? divide_slots(N) : 0;
+        if (slots <= 0) slots = 2 * 152 * 4 / C;  // a bound when the device cannot be asked
+        if (slots > J) slots = J;
+        b += (size_t)slots * 2 * NN * sizeof(float2);
+    }
     if (precision == PTYCHO_PREC_BF16X3) {
         b += (size_t)J * NN * sizeof(float);           // sqrt(I) transposed
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
@@ -330,6 +340,13 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
 
     const int C = divide_cluster_size(N);
     const int chunks = probe_chunks(J, N);
+    {
+        cudaError_t pe = divide_prepare(N);
+        if (pe != cudaSuccess) return cuda_fail(ctx, pe, "divide_prepare");
+    }
+    int n_slots = divide_slots(N);
+    if (n_slots <= 0) n_slots = 1;
+    if (n_slots > J) n_slots = J;
     const int sq_blocks = (int)((NN + 255) / 256);
     double* psum = nullptr;
     int rc;
@@ -343,6 +360,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->x, (size_t)J * NN);
     PT_ALLOC(ctx->y, (size_t)J * NN);
     PT_ALLOC(ctx->sqrtIp, (size_t)J * NN);
+    PT_ALLOC(ctx->scratch, (size_t)n_slots * 2 * NN);
     PT_ALLOC(ctx->P, NN);
     PT_ALLOC(ctx->tw, (size_t)N);
     PT_ALLOC(ctx->O, M);
@@ -380,6 +398,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     ctx->cb.tiles_r = tiles_r;
     ctx->cb.tiles_c = tiles_c;
     ctx->cb.chunks = chunks;
+    ctx->n_slots = n_slots;
     ctx->J = J;
     ctx->N = N;
     ctx->Mr = M_rows;
@@ -481,6 +500,8 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         da.c = c;
         da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;
         da.err_only = 0;
+        da.scratch = ctx->scratch;
+        da.n_slots = ctx->n_slots;
         const bool rec = ctx->prof && ctx->prof_n < kProfMax;
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
         int n_part = ctx->J * ctx->C;
@@ -615,6 +636,8 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
     da.c = 1.f;
     da.write_x = 0;
     da.err_only = 1;
+    da.scratch = ctx->scratch;
+    da.n_slots = ctx->n_slots;
     PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
     PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->J * ctx->C, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
                                   ctx->e_tmp, ctx->stream));
