@@ -323,6 +323,7 @@ def main():
     ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--preset", default="RAAR", choices=["DC", "AR", "DR", "SF", "RAAR", "RRR"])
+    ap.add_argument("--concur", default="deterministic", choices=["deterministic", "atomic"])
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rate", type=float, default=20.0)
     args = ap.parse_args()
@@ -356,7 +357,8 @@ def main():
     J, N = scan.J, scan.N
     # one dedicated stream for the library and for the timing events
     stream = torch.cuda.Stream(device=local)
-    r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
+    r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision,
+                              concur=args.concur)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
     abc = native.PRESETS[args.preset]
     r.iterate(*abc, args.warmup)

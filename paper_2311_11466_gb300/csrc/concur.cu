@@ -48,27 +48,30 @@ __device__ __forceinline__ double block_max_double(double v, double* scratch) {
 }
 
 // Object numerator/denominator by position-tiled gather.  One CTA per
-// 32 x 32 object tile; thread (ty, tx) owns pixels (ty + 8 k, tx), k < 4.
+// kObjTileR x 32 object tile; thread (ty, tx) owns pixels (ty + 8 k, tx)
+// (one pixel per thread with 8-row tiles).
 __global__ void __launch_bounds__(kT) concur_object_kernel(
     const float2* __restrict__ y, const float2* __restrict__ P, const int2* __restrict__ pos,
     const int* __restrict__ tile_ptr, const int* __restrict__ tile_list, int N, int Mr, int Mc,
     int tiles_c, float2* __restrict__ numO, float* __restrict__ denO, unsigned* __restrict__ maxO) {
+    constexpr int KP = kObjTileR / 8;  // pixels per thread
     __shared__ float scratch[kT / 32];
     const int tile = blockIdx.x;
     const int ti = tile / tiles_c, tj = tile % tiles_c;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int mc = tj * kObjTile + tx;
-    const int mr0 = ti * kObjTile + ty;
-    float2 acc[4];
-    float den[4];
+    const int mr0 = ti * kObjTileR + ty;
+    float2 acc[KP];
+    float den[KP];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < KP; ++k) {
         acc[k] = make_float2(0.f, 0.f);
         den[k] = 0.f;
     }
     const size_t NN = (size_t)N * N;
     const int l0 = tile_ptr[tile], l1 = tile_ptr[tile + 1];
-#pragma unroll 2
+    // deep unrolling keeps several windows' loads in flight per thread
+#pragma unroll (8 / KP)
     for (int l = l0; l < l1; ++l) {
         const int j = tile_list[l];
         const int2 s = pos[j];
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
         const bool cin = (unsigned)cc < (unsigned)N;
         const float2* yj = y + (size_t)j * NN;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < KP; ++k) {
             const int rr = mr0 + 8 * k - s.x;
             if (cin && (unsigned)rr < (unsigned)N) {
                 const int o = rr * N + cc;
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
     }
     float mx = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < KP; ++k) {
         const int mr = mr0 + 8 * k;
         if (mr < Mr && mc < Mc) {
             numO[(size_t)mr * Mc + mc] = acc[k];

@@ -47,7 +47,7 @@ template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64
 template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
 template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256, RSM = 9, MINB = 4; };
 template <> struct Cfg<128> { static constexpr int A = 8,  B = 16, C = 4, T = 256, RSM = 9, MINB = 3; };
-template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 8, T = 512, RSM = 1, MINB = 2; };
+template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 16, T = 256, RSM = 1, MINB = 4; };
 
 template <int N>
 struct Geo {
@@ -68,10 +68,21 @@ struct Geo {
 template <int N>
 constexpr bool kRowPerHalfWarp = Geo<N>::A == 16 && Geo<N>::B == 16 && Geo<N>::R * 16 == Geo<N>::T;
 
+// Scratch lines are dropped from L2 once read when a row of the scratch is a
+// whole number of 128-byte lines and the lanes sharing a line sit in one warp.
+template <int N>
+constexpr bool kDiscard = (N % 16 == 0) && (Geo<N>::T % 32 == 0) && (32 % Geo<N>::B == 0);
+
 // One bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
 // multiple of 16); it does not wait and brings nothing into the SM.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Drop a 128-byte line from L2 without writing it back (its contents become
+// undefined); used on scratch lines once every reader has its data.
+__device__ __forceinline__ void discard_l2(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
 template <int N, bool ERR_ONLY>
@@ -131,13 +142,13 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
             const size_t idx = pat + (size_t)r * N + n;
             float2 xv;
             if (load_x) {
-                xv = args.x[idx];
+                xv = __ldcs(args.x + idx);
             } else {
                 const float2 z = cmul_rn(__ldg(args.P + r * N + n), __ldg(Ow + (size_t)r * args.Mc + n));
-                const float2 yv = need_y ? args.y[idx] : make_float2(0.f, 0.f);
-                const float2 xp = need_xp ? args.x[idx] : make_float2(0.f, 0.f);
+                const float2 yv = need_y ? __ldcs(args.y + idx) : make_float2(0.f, 0.f);
+                const float2 xp = need_xp ? __ldcs(args.x + idx) : make_float2(0.f, 0.f);
                 xv = resplit_rn(z, yv, xp, args.pa, args.pb);
-                if (write_x) args.x[idx] = xv;
+                if (write_x) __stcs(args.x + idx, xv);
             }
             v[e] = xv;
         }
@@ -176,6 +187,12 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
         for (int e = 0; e < A; ++e) v[e] = __ldcg(src + B * e);
         dft_reg<A, false>(v);
+        if constexpr (kDiscard<N>) {
+            // the B lanes of row rho (one warp) have read its N / 16 lines of S
+            __syncwarp();
+            const float2* line0 = S + (size_t)(c * R + rho) * N;
+            for (int l = t; l < N / 16; l += B) discard_l2(line0 + 16 * l);
+        }
         float2* p = buf + rho * RS + t;
 #pragma unroll
         for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], twA[k * B + t]);
@@ -268,6 +285,11 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
                 for (int t = 0; t < B; ++t) u[t] = __ldcg(src + t);
             }
+            if constexpr (kDiscard<N>) {
+                // the lanes reading one 128-byte line are in this warp
+                __syncwarp();
+                if ((k * B) % 16 == 0) discard_l2(src);
+            }
             dft_reg<B, true>(u);
             float2* p = buf + row * RS + k * (B + 1);
 #pragma unroll
@@ -287,7 +309,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
             dft_reg<A, true>(v);
             float2* yo = args.y + pat + (size_t)r * N + t;
 #pragma unroll
-            for (int e = 0; e < A; ++e) yo[B * e] = v[e];
+            for (int e = 0; e < A; ++e) __stcs(yo + B * e, v[e]);
         }
     }
 
@@ -345,6 +367,14 @@ cudaError_t prepare_t() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<N>::SMEM);
     if (e != cudaSuccess) return e;
+    if constexpr (Geo<N>::C > 8) {  // clusters above the portable size of 8
+        e = cudaFuncSetAttribute(divide_kernel<N, false>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(divide_kernel<N, true>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(divide_kernel<N, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<N>::SMEM);
 }

@@ -59,7 +59,8 @@ struct ConcurBufs {
     int* tile_list;
     int tiles_r, tiles_c, chunks;
 };
-constexpr int kObjTile = 32;
+constexpr int kObjTileR = 8;   // object tile rows of the gather
+constexpr int kObjTile = 32;   // object tile columns (one warp of pixels)
 int probe_chunks(int J, int N);
 cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
                           const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,

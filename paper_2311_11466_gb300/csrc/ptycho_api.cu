@@ -255,8 +255,8 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     const size_t NN = (size_t)N * N, M = (size_t)M_rows * M_cols;
     const int C = divide_cluster_size(N) > 0 ? divide_cluster_size(N) : 1;
     const size_t chunks = (size_t)probe_chunks(J, N);
-    const int tiles = ((M_rows + kObjTile - 1) / kObjTile) * ((M_cols + kObjTile - 1) / kObjTile);
-    const int tr_per = (N + kObjTile - 1) / kObjTile + 1;
+    const int tiles = ((M_rows + kObjTileR - 1) / kObjTileR) * ((M_cols + kObjTile - 1) / kObjTile);
+    const int tr_per = (N + kObjTileR - 1) / kObjTileR + 1;
     size_t b = 0;
     b += 2 * (size_t)J * NN * sizeof(float2);        // x, y
     b += (size_t)J * NN * sizeof(float);             // sqrt(I)
@@ -317,12 +317,12 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
 
     // Object tiles: CSR lists of the positions whose window overlaps each tile,
     // in ascending position order (integer work, done here).
-    const int tiles_r = (M_rows + kObjTile - 1) / kObjTile;
+    const int tiles_r = (M_rows + kObjTileR - 1) / kObjTileR;
     const int tiles_c = (M_cols + kObjTile - 1) / kObjTile;
     std::vector<int> tile_cnt((size_t)tiles_r * tiles_c + 1, 0);
     for (int j = 0; j < J; ++j) {
         const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
-        for (int ti = r / kObjTile; ti <= (r + N - 1) / kObjTile; ++ti)
+        for (int ti = r / kObjTileR; ti <= (r + N - 1) / kObjTileR; ++ti)
             for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
                 tile_cnt[(size_t)ti * tiles_c + tj + 1]++;
     }
@@ -332,7 +332,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
         std::vector<int> fill(tile_cnt.begin(), tile_cnt.end() - 1);
         for (int j = 0; j < J; ++j) {
             const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
-            for (int ti = r / kObjTile; ti <= (r + N - 1) / kObjTile; ++ti)
+            for (int ti = r / kObjTileR; ti <= (r + N - 1) / kObjTileR; ++ti)
                 for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
                     tile_list[(size_t)fill[(size_t)ti * tiles_c + tj]++] = j;
         }
