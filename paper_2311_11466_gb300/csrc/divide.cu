@@ -15,14 +15,14 @@
 // same order at load time).
 //
 // The two transposes of the 2-D DFT (row pass -> column pass and back) go
-// through a small scratch area in global memory, one slot of 2 N^2 complex
-// per cluster: the row pass's second half stores its outputs there in the
+// through global memory: the row pass's second half stores its outputs in the
 // column-major order the other CTAs need, one cluster barrier (release /
 // acquire, cluster scope) later the column pass reads them straight into
-// registers (L2-cached loads); the inverse goes back the same way.  Clusters
-// are persistent (as many as fit on the GPU at once, each looping over exit
-// waves), so every cluster keeps reusing its own slot and the scratch stays
-// resident in L2.  Two cluster barriers per exit wave.
+// registers (L2-cached loads), then drops the lines from L2 without a write
+// back; the inverse goes back the same way through the exit wave's own y
+// buffer.  Two cluster barriers per exit wave; one cluster per exit wave, so
+// clusters start as others finish and their memory and compute phases
+// interleave on each SM.
 //
 // Shared-memory row layout: element t + B e of a row lives at slot e (B + 1) + t
 // so both passes are bank-conflict free; the row stride RS keeps the passes
@@ -100,11 +100,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
     const int tid = threadIdx.x;
-    const int slot = (int)(blockIdx.x / C);
-    const int n_clusters = (int)(gridDim.x / C);
-    // the cluster's scratch: S[v'][r] (row pass -> column pass), S2[r][v'] (back)
-    float2* S = args.scratch + (size_t)slot * 2 * NN;
-    float2* S2 = S + NN;
+    const int j = (int)(blockIdx.x / C);  // one cluster per exit wave
 
     for (int i = tid; i < N; i += T) {
         const float2 w = args.tw[i];
@@ -115,9 +111,13 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     const bool load_x = args.load_x != 0, write_x = args.write_x != 0;
     const bool need_y = args.pb != 1.0f, need_xp = args.pa != 1.0f;
 
-#pragma unroll 1
-    for (int j = slot; j < args.J; j += n_clusters) {
     const size_t pat = (size_t)j * NN;
+    // transpose scratch: S[v'][r] (row pass -> column pass) in this wave's
+    // scratch buffer; S2[r][v'] (back) in its y buffer, which holds nothing
+    // live between the re-split's read of y_{k-1} (before the first cluster
+    // barrier) and the store of y_k (after the second)
+    float2* S = args.scratch + pat;
+    float2* S2 = args.y + pat;
     if (tid == 0) {
         // stream this CTA's rows of x, y and sqrt(I) into L2 at once
         const size_t off = pat + (size_t)c * R * N;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         if (!load_x && need_y) prefetch_l2(args.y + off, cbytes);
         prefetch_l2(args.sqrtIp + off, (unsigned)(R * N * sizeof(float)));
     }
-    __syncthreads();  // twiddles loaded / the previous wave's shared-memory reads done
+    __syncthreads();  // twiddles loaded
     const int2 s = args.pos[j];
     const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
 
@@ -325,10 +325,6 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         for (int w = 0; w < T / 32; ++w) tot += redf[w];
         args.e_part[(size_t)j * C + c] = (double)tot;
     }
-    // without the inverse half (error only), the next wave's row pass must not
-    // overwrite S before every CTA has read it
-    if constexpr (ERR_ONLY) cl.sync();
-    }  // exit waves
 }
 
 template <int N>
@@ -383,8 +379,7 @@ template <int N>
 cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     using G = Geo<N>;
     cudaLaunchConfig_t cfg = {};
-    const int clusters = a.J < a.n_slots ? a.J : a.n_slots;
-    cfg.gridDim = dim3((unsigned)clusters * G::C);
+    cfg.gridDim = dim3((unsigned)a.J * G::C);
     cfg.blockDim = dim3(G::T);
     cfg.dynamicSmemBytes = G::SMEM;
     cfg.stream = st;

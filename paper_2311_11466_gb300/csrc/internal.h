@@ -25,8 +25,8 @@ struct DivideArgs {
     float c;              // divide relaxation
     int write_x;          // store x_k to x[] (needed when this iteration's a != 1)
     int err_only;         // only the Fourier error of x_k (no y written)
-    float2* scratch;      // [n_slots][2 N^2] transpose scratch, one slot per resident cluster
-    int n_slots;
+    float2* scratch;      // [J][N^2] transpose scratch (row pass -> column pass)
+    int n_slots;          // unused by the kernel (kept for the launch helpers)
 };
 
 // Supported pattern sides.

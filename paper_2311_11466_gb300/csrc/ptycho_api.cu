@@ -268,12 +268,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += NN * (sizeof(double2) + sizeof(double));
     b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
-    {
-        int slots = divide_supported(N) && divide_prepare(N) == cudaSuccess ? divide_slots(N) : 0;
-        if (slots <= 0) slots = 2 * 152 * 4 / C;  // a bound when the device cannot be asked
-        if (slots > J) slots = J;
-        b += (size_t)slots * 2 * NN * sizeof(float2);
-    }
+    b += (size_t)J * NN * sizeof(float2);  // transpose scratch
     if (precision == PTYCHO_PREC_BF16X3) {
         b += (size_t)J * NN * sizeof(float);           // sqrt(I) transposed
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
@@ -360,7 +355,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->x, (size_t)J * NN);
     PT_ALLOC(ctx->y, (size_t)J * NN);
     PT_ALLOC(ctx->sqrtIp, (size_t)J * NN);
-    PT_ALLOC(ctx->scratch, (size_t)n_slots * 2 * NN);
+    PT_ALLOC(ctx->scratch, (size_t)J * NN);
     PT_ALLOC(ctx->P, NN);
     PT_ALLOC(ctx->tw, (size_t)N);
     PT_ALLOC(ctx->O, M);
