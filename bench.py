@@ -310,6 +310,36 @@ def run_serve_mode(args):
     return 0
 
 
+def run_compare_mode(args):
+    """The shape of the paper's comparison (Figs. 6-8): every (a, b, c) setting,
+    a big and a small probe on the same synthetic object and scan, Fourier
+    error per iteration and the final ambiguity-corrected object error."""
+    from paper_2311_11466_gb300 import build as _build, metrics, native, synth
+    _build.build()
+    iters = args.e2e_iters
+    out = {}
+    for label, radius in (("big", 32.0), ("small", 16.0)):
+        spec = synth.ScanSpec(N=128, ny=12, nx=12, step=16, jitter=2, radius=radius,
+                              defocus=0.02 * (16.0 / radius) ** 2, photons=1e6, seed=6)
+        scan = synth.make_scan(spec)
+        rows = {}
+        for name in ["DC", "AR", "DR", "SF", "RAAR", "RRR"]:
+            with native.Reconstruction() as r:
+                r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+                r.iterate(*native.PRESETS[name], iters)
+                e = r.errors()
+                O, _ = r.object_probe()
+                rows[name] = {"E_F": {str(k): float(e[k - 1]) for k in (1, 10, 50, 100, iters) if k <= iters},
+                              "model_E_F": r.model_error(),
+                              "object_error": metrics.object_error(O, scan.obj_true, scan.N)}
+        out[label] = {"probe_radius": radius, "J": scan.J, "N": scan.N, "M": list(scan.M_shape),
+                      "results": rows}
+    line = {"metric": "error after iterations, every preset, big vs small probe", "mode": "compare",
+            "iterations": iters, "data": "synthetic", "dtype": "f32", "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,7 +350,7 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve"])
+    ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve", "compare"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--preset", default="RAAR", choices=["DC", "AR", "DR", "SF", "RAAR", "RRR"])
     ap.add_argument("--concur", default="deterministic", choices=["deterministic", "atomic"])
@@ -331,6 +361,8 @@ def main():
         return run_batch_mode(args)
     if args.mode == "serve":
         return run_serve_mode(args)
+    if args.mode == "compare":
+        return run_compare_mode(args)
 
     from paper_2311_11466_gb300 import synth
     if args.precision == "bf16x3" and args.workload == "large":

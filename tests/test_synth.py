@@ -58,3 +58,19 @@ def test_fermat_and_batch_specs():
     p = s.pos.astype(float)
     d = np.sqrt(((p[:, None] - p[None]) ** 2).sum(-1)) + np.eye(len(p)) * 1e9
     assert 4 < d.min(axis=1).mean() < 12
+
+
+def test_product_object_error_matches_oracle():
+    # the library's own object-error metric (used by the benchmark) against the
+    # oracle's independent implementation of the same reading
+    from oracle import metrics as om
+    from paper_2311_11466_gb300 import metrics as pm
+    s = synth.make_scan(synth.named_spec("tiny"))
+    rng = np.random.default_rng(3)
+    rr, cc = np.meshgrid(np.arange(176), np.arange(176), indexing="ij")
+    for trial in range(3):
+        O = (0.7 - 0.3j) * np.exp(2j * np.pi * (rr * 5 / 896 + cc * 2 / 896)) * s.obj_true
+        O = O + 0.05 * trial * (rng.standard_normal(O.shape) + 1j * rng.standard_normal(O.shape))
+        a, b = pm.object_error(O, s.obj_true, s.N), om.object_error(O, s.obj_true, s.N)
+        assert abs(a - b) <= 1e-12 + 1e-9 * b
+    assert pm.object_error(0 * s.obj_true, s.obj_true, s.N) == 1.0
