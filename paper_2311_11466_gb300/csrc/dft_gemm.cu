@@ -22,11 +22,13 @@
 // re-split of the previous iteration, exactly as the FP32 kernel does) and
 // writes its hi/lo planes.
 //
-// GEMM kernel: one CTA per 128 x 256 output tile (128 rows x 128 complex
-// columns) of one exit wave; warp 0 issues TMA loads (128-byte swizzle) into
-// a 4-stage shared-memory ring, warp 1 allocates 256 tensor-memory columns
+// GEMM kernel: persistent, one CTA per SM looping over 128 x 256 output tiles
+// (128 rows x 128 complex columns of one exit wave); warp 0 issues TMA loads
+// (128-byte swizzle) into a 4-stage shared-memory ring that runs on across
+// tiles, warp 1 allocates all 512 tensor-memory columns (two accumulators)
 // and issues tcgen05.mma (M = 128, N = 256, K = 16) from one thread, warps
-// 2-5 read the accumulator with tcgen05.ld and run the epilogue.  Every wait
+// 2-5 drain one accumulator with tcgen05.ld and run the epilogue while the
+// MMAs of the next tile fill the other.  Every wait
 // on an mbarrier is bounded in time; on expiry the kernel records an error
 // flag, drains and returns (the host reports PTYCHO_ETIMEOUT).
 #include <cuda.h>
@@ -174,35 +176,35 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t sA = base + pad;                                   // [stages][16 KiB]
     const uint32_t sB = sA + kStages * kABytes;                       // [stages][32 KiB]
     unsigned char* tail = sm + kStages * (kABytes + kBBytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tail);               // full[S], empty[S], done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
-    double* red = reinterpret_cast<double*>(tail + 128);              // 4 doubles
+    // full[S], empty[S], acc_full[2], acc_empty[2], then the TMEM address
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
 
     const int N = g.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt_per = N / kBM, nt_per = (2 * N) / kBN;
     const int tiles_per = mt_per * nt_per;
-    const int j = blockIdx.x / tiles_per;
-    const int t_in = blockIdx.x % tiles_per;
-    const int mt = t_in / nt_per, nt = t_in % nt_per;
-    const int row0 = j * N + mt * kBM;  // row in the [J*N][2N] operand
+    const int tiles = g.J * tiles_per;
     const int KBP = (2 * N) / kBK;      // k-blocks per product
     const int KB = 3 * KBP;             // hi*hi, hi*lo, lo*hi
 
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages),
-                   done = smem_u32(bars + 2 * kStages);
+                   afull0 = smem_u32(bars + 2 * kStages), aempty0 = smem_u32(bars + 2 * kStages + 2);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(afull0 + 8 * b, 1);   // one tcgen05.commit
+            mbar_init(aempty0 + 8 * b, 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(2 * kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -212,57 +214,78 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % kStages;
-            const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, g.err_flag)) break;
-            mbar_expect_tx(full0 + 8 * s, kABytes + kBBytes);
-            const int pair = kb / KBP, kin = (kb % KBP) * kBK;
-            tma_load_2d(sA + s * kABytes, pair == 2 ? &mapAlo : &mapAhi, kin, row0, full0 + 8 * s);
-            tma_load_2d(sB + s * kBBytes, pair == 1 ? &mapBlo : &mapBhi, kin, nt * kBN, full0 + 8 * s);
+        // producer: the stage ring runs on across tiles
+        uint32_t gk = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const int j = t / tiles_per, t_in = t % tiles_per;
+            const int mt = t_in / nt_per, nt = t_in % nt_per;
+            const int row0 = j * N + mt * kBM;
+            for (int kb = 0; kb < KB; ++kb, ++gk) {
+                const uint32_t s = gk % kStages, ph = (gk / kStages) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, g.err_flag)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(full0 + 8 * s, kABytes + kBBytes);
+                const int pair = kb / KBP, kin = (kb % KBP) * kBK;
+                tma_load_2d(sA + s * kABytes, pair == 2 ? &mapAlo : &mapAhi, kin, row0, full0 + 8 * s);
+                tma_load_2d(sB + s * kBBytes, pair == 1 ? &mapBlo : &mapBhi, kin, nt * kBN, full0 + 8 * s);
+            }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
+        // MMA issuer: accumulator i & 1 of the i-th tile of this CTA
+        uint32_t gk = 0;
         bool ok = true;
-        for (int kb = 0; kb < KB && ok; ++kb) {
-            const int s = kb % kStages;
-            const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-            ok = mbar_wait(full0 + 8 * s, ph, g.err_flag);
-            if (!ok) break;
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+            const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
+            if (!mbar_wait(aempty0 + 8 * ab, aph ^ 1u, g.err_flag)) break;  // epilogue done with it
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + ab * kTmemCols;
+            for (int kb = 0; kb < KB; ++kb, ++gk) {
+                const uint32_t s = gk % kStages, ph = (gk / kStages) & 1u;
+                if (!mbar_wait(full0 + 8 * s, ph, g.err_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint64_t ad = desc_sw128(sA + s * kABytes + kk * 32);
-                const uint64_t bd = desc_sw128(sB + s * kBBytes + kk * 32);
-                mma_bf16(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint64_t ad = desc_sw128(sA + s * kABytes + kk * 32);
+                    const uint64_t bd = desc_sw128(sB + s * kBBytes + kk * 32);
+                    mma_bf16(acc, ad, bd, (kb | kk) != 0 ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs complete
             }
-            mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs complete
+            mma_commit(afull0 + 8 * ab);     // the accumulator is complete
         }
-        mma_commit(done);
     } else if (warp >= 2) {
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
         const int q = warp & 3;
-        const int rloc = 32 * q + lane;    // tile row
-        const int m = mt * kBM + rloc;     // row within the exit wave
-        float err = 0.f;
-        const bool ok = mbar_wait(done, 0, g.err_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-            const size_t NN = (size_t)N * N;
-            const float inv_n2 = 1.0f / (float)(N * N);
-            const float cr = g.c, oc = 1.0f - g.c;
+        const size_t NN = (size_t)N * N;
+        const float inv_n2 = 1.0f / (float)(N * N);
+        const float cr = g.c, oc = 1.0f - g.c;
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int j = t / tiles_per, t_in = t % tiles_per;
+            const int mt = t_in / nt_per, nt = t_in % nt_per;
+            const int m = mt * kBM + 32 * q + lane;  // row within the exit wave
+            const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
+            if (!mbar_wait(afull0 + 8 * ab, aph, g.err_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float err = 0.f;
 #pragma unroll 1
             for (int ch = 0; ch < kBN / 32; ++ch) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * ch), r);
+                tmem_ld32(tmem + ab * kTmemCols + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * ch), r);
                 const int v0 = nt * (kBN / 2) + 16 * ch;  // first complex column of the chunk
                 if constexpr (EPI == kEpiSplitT) {
                     // next operand row v, column m (re) and N + m (im)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
-                        const size_t o = ((size_t)j * N + v0 + i) * (2 * N) + m;
+                    for (int ii = 0; ii < 16; ++ii) {
+                        const float re = __uint_as_float(r[2 * ii]), im = __uint_as_float(r[2 * ii + 1]);
+                        const size_t o = ((size_t)j * N + v0 + ii) * (2 * N) + m;
                         __nv_bfloat16 h, l;
                         split_bf16(re, h, l);
                         g.out_hi[o] = h;
@@ -276,9 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float* sq = g.sqrtIt + (size_t)j * NN + (size_t)m * N + v0;
                     alignas(16) __nv_bfloat16 hr[16], hi_[16], lr[16], li[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float re = __uint_as_float(r[2 * i]), im = __uint_as_float(r[2 * i + 1]);
-                        const float sv = __ldg(sq + i);
+                    for (int ii = 0; ii < 16; ++ii) {
+                        const float re = __uint_as_float(r[2 * ii]), im = __uint_as_float(r[2 * ii + 1]);
+                        const float sv = __ldg(sq + ii);
                         const float m2 = fmaf(re, re, im * im);
                         const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
                         const float d = fmaf(m2, rs, -sv);
@@ -286,8 +309,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float gsc = (cr * sv) * rs + oc;
                         const float pre = m2 > 0.f ? re * (gsc * inv_n2) : cr * sv * inv_n2;
                         const float pim = m2 > 0.f ? im * (gsc * inv_n2) : 0.f;
-                        split_bf16(pre, hr[i], lr[i]);
-                        split_bf16(pim, hi_[i], li[i]);
+                        split_bf16(pre, hr[ii], lr[ii]);
+                        split_bf16(pim, hi_[ii], li[ii]);
                     }
                     const size_t o = ((size_t)j * N + m) * (2 * N) + v0;
                     uint4* dh = reinterpret_cast<uint4*>(g.out_hi + o);
@@ -303,31 +326,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     dli[0] = reinterpret_cast<const uint4*>(li)[0];
                     dli[1] = reinterpret_cast<const uint4*>(li)[1];
                 } else {
-                    // y[j][m][v0 + i]
+                    // y[j][m][v0 + ii]
                     float4* yo = reinterpret_cast<float4*>(g.y + (size_t)j * NN + (size_t)m * N + v0);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        yo[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
-                                            __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                    for (int ii = 0; ii < 8; ++ii)
+                        yo[ii] = make_float4(__uint_as_float(r[4 * ii]), __uint_as_float(r[4 * ii + 1]),
+                                             __uint_as_float(r[4 * ii + 2]), __uint_as_float(r[4 * ii + 3]));
                 }
             }
-        }
-        if constexpr (EPI == kEpiModulus) {
-            double e = (double)err;
+            // hand the accumulator back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0 + 8 * ab) : "memory");
+            }
+            if constexpr (EPI == kEpiModulus) {
+                float e = err;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-            if (lane == 0) red[q] = e;
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+                if (lane == 0) g.e_part[(size_t)t * 4 + q] = (double)e;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if constexpr (EPI == kEpiModulus) {
-        if (threadIdx.x == 0) g.e_part[blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
-    }
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
+                     "r"(2 * kTmemCols)
                      : "memory");
     }
 }
@@ -426,6 +452,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, ui
 bool bf16x3_supported(int N) { return N == 128 || N == 256; }
 
 int bf16x3_tiles(int N, int J) { return J * (N / kBM) * ((2 * N) / kBN); }
+int bf16x3_error_parts(int N, int J) { return 4 * bf16x3_tiles(N, J); }  // one per epilogue warp and tile
 
 // The constant B operands (K-major, output columns interleaved re/im), hi and
 // lo parts: fwd for F, inv for conj(F).  Layout [2N rows (output)][2N (k)].
@@ -507,20 +534,28 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt
     g.err_flag = err_flag;
     g.y = a.y;
     const int tiles = bf16x3_tiles(N, a.J);
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
+            n_sm = 148;
+    }
+    const int grid = tiles < n_sm ? tiles : n_sm;  // persistent: one CTA per SM
     // 1: Z = X F -> Z^T into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    dft_gemm_kernel<kEpiSplitT><<<tiles, kThreads, kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], g);
+    dft_gemm_kernel<kEpiSplitT><<<grid, kThreads, kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], g);
     // 2: Psi^T = Z^T F, modulus -> Psi''^T into buffer 0
     g.out_hi = p[0];
     g.out_lo = p[1];
-    dft_gemm_kernel<kEpiModulus><<<tiles, kThreads, kSmem, st>>>(mA[2], mA[3], mB[0], mB[1], g);
+    dft_gemm_kernel<kEpiModulus><<<grid, kThreads, kSmem, st>>>(mA[2], mA[3], mB[0], mB[1], g);
     // 3: G^T = Psi''^T conj(F) -> G into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    dft_gemm_kernel<kEpiSplitT><<<tiles, kThreads, kSmem, st>>>(mA[0], mA[1], mB[2], mB[3], g);
+    dft_gemm_kernel<kEpiSplitT><<<grid, kThreads, kSmem, st>>>(mA[0], mA[1], mB[2], mB[3], g);
     // 4: y = G conj(F)
-    dft_gemm_kernel<kEpiOut><<<tiles, kThreads, kSmem, st>>>(mA[2], mA[3], mB[2], mB[3], g);
+    dft_gemm_kernel<kEpiOut><<<grid, kThreads, kSmem, st>>>(mA[2], mA[3], mB[2], mB[3], g);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* o
 // Tensor-core (BF16 x 3) divide path (dft_gemm.cu).
 bool bf16x3_supported(int N);
 int bf16x3_tiles(int N, int J);
+int bf16x3_error_parts(int N, int J);
 void bf16x3_constants(int N, std::vector<uint16_t>& fwd_hi, std::vector<uint16_t>& fwd_lo,
                       std::vector<uint16_t>& inv_hi, std::vector<uint16_t>& inv_lo);
 cudaError_t bf16x3_prepare();

@@ -274,7 +274,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
         b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
         b += (size_t)J * (NN / 1024 + 1) * sizeof(double);
-        const size_t tiles = (size_t)J * (N / 128 > 0 ? (N / 128) * (N / 128) : 1);
+        const size_t tiles = 4 * (size_t)J * (N / 128 > 0 ? (N / 128) * (N / 128) : 1);
         if (tiles > (size_t)J * C) b += (tiles - (size_t)J * C) * sizeof(double);
     }
     return b;
@@ -382,7 +382,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->Bc[i], 4 * NN);
         PT_ALLOC(psum_t, (size_t)J * (NN / 1024));
-        const int tiles = bf16x3_tiles(N, J);
+        const int tiles = bf16x3_error_parts(N, J);
         if (tiles > J * C) {
             double* more = nullptr;
             PT_ALLOC(more, (size_t)tiles);
@@ -503,7 +503,7 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         if (ctx->opts.precision == PTYCHO_PREC_BF16X3) {
             PT_CUDA(ctx, launch_divide_bf16x3(da, ctx->N, ctx->sqrtIt, ctx->planes, ctx->Bc,
                                               ctx->dflag + 1, ctx->stream));
-            n_part = bf16x3_tiles(ctx->N, ctx->J);
+            n_part = bf16x3_error_parts(ctx->N, ctx->J);
         } else {
             PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
         }
