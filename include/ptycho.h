@@ -116,6 +116,19 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
  * Errors: EINVAL (a, b, c not finite, n_iter < 0), ESTATE (no scan), ECUDA. */
 int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter);
 
+/* Sequential projections (Introduction, Fig. 2): n_iter passes over the
+ * positions, each position visited once per pass in the order given
+ * (order: host int32 [J], a permutation of 0..J-1, or NULL for ascending).
+ * At position j, with psi = P * O_j and psi' = lam P_{S_j}(psi) + (1 - lam) psi
+ * (S_j the Fourier-modulus set of position j):
+ *     O_j += conj(P) (psi' - psi) / max|P|^2,   P += conj(O_j) (psi' - psi) / max|O_j|^2
+ * (O_j before its update on the right).  Appends the Fourier error of each
+ * pass to the error history; afterwards the exit waves are P * O_j, so an
+ * abc iteration can continue from the result.  Asynchronous.
+ * Errors: EINVAL (lam not finite, n_iter < 0, order not a permutation),
+ * ESTATE (no scan), ECUDA. */
+int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t n_iter);
+
 /* Copy the current object [M_rows][M_cols][2] and probe [N][N][2] to host
  * buffers (either may be NULL).  Synchronises.  Errors: ESTATE, ECUDA. */
 int ptycho_get_object_probe(ptycho_ctx* ctx, float* obj_out, float* probe_out);

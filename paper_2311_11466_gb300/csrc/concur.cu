@@ -227,6 +227,21 @@ __global__ void __launch_bounds__(kT) sum_parts_kernel(const double* __restrict_
     if (threadIdx.x == 0) *out = tot * scale;
 }
 
+__global__ void __launch_bounds__(kT) record_error_kernel(const double* __restrict__ parts, int n,
+                                                          double scale, double* __restrict__ ring,
+                                                          unsigned long long* __restrict__ d_iter,
+                                                          int cap) {
+    __shared__ double scratch[kT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kT) s += parts[i];
+    const double tot = block_sum_double<kT>(s, scratch);
+    if (threadIdx.x == 0) {
+        const unsigned long long k = *d_iter;
+        ring[k % (unsigned long long)cap] = tot * scale;
+        *d_iter = k + 1;
+    }
+}
+
 __global__ void __launch_bounds__(kT) form_waves_kernel(float2* __restrict__ x,
                                                         const float2* __restrict__ P,
                                                         const float2* __restrict__ O,
@@ -298,6 +313,12 @@ cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos
                                                              (double)alpha, P, e_part, n_part,
                                                              inv_sumI, e_ring, d_iter, ring_cap,
                                                              cb.maxO);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record_error(const double* parts, int n, double scale, double* ring,
+                                unsigned long long* d_iter, int cap, cudaStream_t st) {
+    record_error_kernel<<<1, kT, 0, st>>>(parts, n, scale, ring, d_iter, cap);
     return cudaGetLastError();
 }
 

@@ -85,8 +85,14 @@ __device__ __forceinline__ void discard_l2(const void* p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-template <int N, bool ERR_ONLY>
+// Kernel modes: the divide step; the Fourier error only; one step of
+// sequential projections (update O and P from one exit wave).
+enum : int { kModeDivide = 0, kModeErrOnly = 1, kModeSP = 2 };
+
+template <int N, int MODE>
 __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const DivideArgs args) {
+    constexpr bool ERR_ONLY = MODE == kModeErrOnly;
+    constexpr bool SP = MODE == kModeSP;
     using G = Geo<N>;
     constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS;
     constexpr int TP2 = G::TP2;
@@ -100,7 +106,9 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
     const int tid = threadIdx.x;
-    const int j = (int)(blockIdx.x / C);  // one cluster per exit wave
+    // one cluster per exit wave; a sequential-projections step works on one
+    // given position
+    const int j = SP ? args.sp_pos : (int)(blockIdx.x / C);
 
     for (int i = tid; i < N; i += T) {
         const float2 w = args.tw[i];
@@ -116,8 +124,8 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     // scratch buffer; S2[r][v'] (back) in its y buffer, which holds nothing
     // live between the re-split's read of y_{k-1} (before the first cluster
     // barrier) and the store of y_k (after the second)
-    float2* S = args.scratch + pat;
-    float2* S2 = args.y + pat;
+    float2* S = SP ? args.scratch : args.scratch + pat;
+    float2* S2 = SP ? args.scratch + NN : args.y + pat;  // SP leaves y untouched
     if (tid == 0) {
         // stream this CTA's rows of x, y and sqrt(I) into L2 at once
         const size_t off = pat + (size_t)c * R * N;
@@ -129,6 +137,46 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     __syncthreads();  // twiddles loaded
     const int2 s = args.pos[j];
     const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
+
+    // Sequential projections, phase 0: max |P|^2 over the probe and max |O_j|^2
+    // over the window, each CTA over its rows, then across the cluster.
+    float inv_maxP = 0.f, inv_maxO = 0.f;
+    if constexpr (SP) {
+        float mp = 0.f, mo = 0.f;
+        for (int e = tid; e < R * N; e += T) {
+            const int r = c * R + e / N, n = e % N;
+            mp = fmaxf(mp, cabs2(args.P[r * N + n]));
+            mo = fmaxf(mo, cabs2(Ow[(size_t)r * args.Mc + n]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+            mo = fmaxf(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+        }
+        if ((tid & 31) == 0) {
+            redf[2 * (tid >> 5)] = mp;
+            redf[2 * (tid >> 5) + 1] = mo;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < T / 32; ++w) {
+                mp = fmaxf(mp, redf[2 * w]);
+                mo = fmaxf(mo, redf[2 * w + 1]);
+            }
+            redf[62] = mp;  // this CTA's maxima, read by the whole cluster
+            redf[63] = mo;
+        }
+        cl.sync();
+        mp = 0.f;
+        mo = 0.f;
+        for (int q = 0; q < C; ++q) {
+            const float* rq = cl.map_shared_rank(redf, q);
+            mp = fmaxf(mp, rq[62]);
+            mo = fmaxf(mo, rq[63]);
+        }
+        inv_maxP = mp > 0.f ? 1.0f / mp : 0.f;
+        inv_maxO = mo > 0.f ? 1.0f / mo : 0.f;
+    }
 
     // Phase 1: form x_k, row DFT pass 1 (lanes over t).
 #pragma unroll 1
@@ -307,9 +355,23 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
             for (int k = 0; k < A; ++k) v[k] = p[k * (B + 1)];
             dft_reg<A, true>(v);
-            float2* yo = args.y + pat + (size_t)r * N + t;
+            if constexpr (SP) {
+                // d = psi' - psi; O_j += conj(P) d / max|P|^2, P += conj(O_j) d / max|O_j|^2
 #pragma unroll
-            for (int e = 0; e < A; ++e) __stcs(yo + B * e, v[e]);
+                for (int e = 0; e < A; ++e) {
+                    const int n = t + B * e;
+                    const float2 pv = args.P[r * N + n];
+                    float2* op = args.O_mut + (size_t)(s.x + r) * args.Mc + s.y + n;
+                    const float2 ov = *op;
+                    const float2 d = csub(v[e], cmul_rn(pv, ov));
+                    *op = cadd(ov, cscale(cconjmul(pv, d), inv_maxP));
+                    args.P_mut[r * N + n] = cadd(pv, cscale(cconjmul(ov, d), inv_maxO));
+                }
+            } else {
+                float2* yo = args.y + pat + (size_t)r * N + t;
+#pragma unroll
+                for (int e = 0; e < A; ++e) __stcs(yo + B * e, v[e]);
+            }
         }
     }
 
@@ -359,19 +421,25 @@ __global__ void __launch_bounds__(256) sqrt_permute_kernel(const float* __restri
 
 template <int N>
 cudaError_t prepare_t() {
-    cudaError_t e = cudaFuncSetAttribute(divide_kernel<N, false>,
+    cudaError_t e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<N>::SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(divide_kernel<N, kModeSP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<N>::SMEM);
+    if (e != cudaSuccess) return e;
     if constexpr (Geo<N>::C > 8) {  // clusters above the portable size of 8
-        e = cudaFuncSetAttribute(divide_kernel<N, false>,
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(divide_kernel<N, true>,
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeSP>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute(divide_kernel<N, true>,
+    return cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<N>::SMEM);
 }
 
@@ -390,8 +458,12 @@ cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (a.err_only) return cudaLaunchKernelEx(&cfg, divide_kernel<N, true>, a);
-    return cudaLaunchKernelEx(&cfg, divide_kernel<N, false>, a);
+    if (a.sp) {
+        cfg.gridDim = dim3((unsigned)G::C);  // one cluster: one position
+        return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeSP>, a);
+    }
+    if (a.err_only) return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeErrOnly>, a);
+    return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeDivide>, a);
 }
 
 template <int N>
@@ -468,7 +540,7 @@ int slots_t() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, divide_kernel<N, false>, &cfg) != cudaSuccess || n <= 0) {
+    if (cudaOccupancyMaxActiveClusters(&n, divide_kernel<N, kModeDivide>, &cfg) != cudaSuccess || n <= 0) {
         cudaGetLastError();
         n = 0;
     }

@@ -27,6 +27,10 @@ struct DivideArgs {
     int err_only;         // only the Fourier error of x_k (no y written)
     float2* scratch;      // [J][N^2] transpose scratch (row pass -> column pass)
     int n_slots;          // unused by the kernel (kept for the launch helpers)
+    int sp;               // 1: one sequential-projections step (at position sp_pos)
+    int sp_pos;
+    float2* P_mut;        // probe and object updated by a sequential-projections step
+    float2* O_mut;
 };
 
 // Supported pattern sides.
@@ -74,6 +78,9 @@ cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, cons
                                cudaStream_t st);
 cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
                              cudaStream_t st);
+// FP64 sum of parts times scale into ring[*d_iter % cap], then ++*d_iter.
+cudaError_t launch_record_error(const double* parts, int n, double scale, double* ring,
+                                unsigned long long* d_iter, int cap, cudaStream_t st);
 
 // Tensor-core (BF16 x 3) divide path (dft_gemm.cu).
 bool bf16x3_supported(int N);

@@ -268,7 +268,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += NN * (sizeof(double2) + sizeof(double));
     b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
-    b += (size_t)J * NN * sizeof(float2);  // transpose scratch
+    b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
     if (precision == PTYCHO_PREC_BF16X3) {
         b += (size_t)J * NN * sizeof(float);           // sqrt(I) transposed
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
@@ -355,7 +355,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->x, (size_t)J * NN);
     PT_ALLOC(ctx->y, (size_t)J * NN);
     PT_ALLOC(ctx->sqrtIp, (size_t)J * NN);
-    PT_ALLOC(ctx->scratch, (size_t)J * NN);
+    PT_ALLOC(ctx->scratch, (size_t)(J > 2 ? J : 2) * NN);  // SP steps use two slots
     PT_ALLOC(ctx->P, NN);
     PT_ALLOC(ctx->tw, (size_t)N);
     PT_ALLOC(ctx->O, M);
@@ -643,6 +643,67 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
 }
 
 size_t ptycho_device_bytes(const ptycho_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t n_iter) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!std::isfinite(lam)) return fail(ctx, PTYCHO_EINVAL, "lam must be finite");
+    if (n_iter < 0) return fail(ctx, PTYCHO_EINVAL, "n_iter must be >= 0");
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    std::vector<int32_t> ord((size_t)ctx->J);
+    if (order) {
+        std::vector<char> seen((size_t)ctx->J, 0);
+        for (int i = 0; i < ctx->J; ++i) {
+            const int32_t v = order[i];
+            if (v < 0 || v >= ctx->J || seen[(size_t)v])
+                return fail(ctx, PTYCHO_EINVAL, "order is not a permutation of 0..J-1");
+            seen[(size_t)v] = 1;
+            ord[(size_t)i] = v;
+        }
+    } else {
+        for (int i = 0; i < ctx->J; ++i) ord[(size_t)i] = i;
+    }
+    if (n_iter == 0) return PTYCHO_OK;
+    DeviceGuard dg(ctx->opts.device);
+    const double inv_sumI = ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0;
+    DivideArgs da{};
+    da.x = ctx->x;
+    da.y = ctx->y;
+    da.sqrtIp = ctx->sqrtIp;
+    da.P = ctx->P;
+    da.O = ctx->O;
+    da.P_mut = ctx->P;
+    da.O_mut = ctx->O;
+    da.pos = ctx->pos;
+    da.tw = ctx->tw;
+    da.e_part = ctx->e_part;
+    da.J = ctx->J;
+    da.Mc = ctx->Mc;
+    da.load_x = 0;
+    da.pa = 1.f;  // the exit wave P * O_j
+    da.pb = 1.f;
+    da.c = lam;
+    da.write_x = 0;
+    da.err_only = 0;
+    da.scratch = ctx->scratch;
+    da.n_slots = ctx->n_slots;
+    da.sp = 1;
+    for (int it = 0; it < n_iter; ++it) {
+        for (int i = 0; i < ctx->J; ++i) {
+            da.sp_pos = ord[(size_t)i];
+            PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+        }
+        PT_CUDA(ctx, launch_record_error(ctx->e_part, ctx->J * ctx->C, inv_sumI, ctx->e_ring,
+                                         ctx->d_iter, kRing, ctx->stream));
+        ctx->iters++;
+    }
+    // the product-space iterate follows the new object and probe
+    PT_CUDA(ctx, launch_form_waves(ctx->x, ctx->P, ctx->O, ctx->pos, ctx->J, ctx->N, ctx->Mc,
+                                   ctx->stream));
+    ctx->have_x = true;
+    ctx->pa = ctx->pb = 1.f;
+    return PTYCHO_OK;
+}
 
 int ptycho_profile_enable(ptycho_ctx* ctx, int enable) {
     if (!ctx) return PTYCHO_EINVAL;

@@ -69,6 +69,7 @@ _SIGS = {
     "ptycho_load_scan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                         ctypes.c_int32, _P, _P, ctypes.c_uint32]),
     "ptycho_iterate": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int32]),
+    "ptycho_sp_iterate": (ctypes.c_int, [_P, ctypes.c_float, _P, ctypes.c_int32]),
     "ptycho_get_object_probe": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_set_object_probe": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_get_exit_waves": (ctypes.c_int, [_P, _P]),
@@ -170,6 +171,11 @@ def ptycho_load_scan(h, pos, intensity, obj0, probe0) -> None:
 
 def ptycho_iterate(h, a: float, b: float, c: float, n_iter: int) -> None:
     _check(lib().ptycho_iterate(h, a, b, c, n_iter), h)
+
+
+def ptycho_sp_iterate(h, lam: float, order, n_iter: int) -> None:
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    _check(lib().ptycho_sp_iterate(h, lam, _ptr(o), n_iter), h)
 
 
 def ptycho_get_object_probe(h, obj_out: np.ndarray | None, probe_out: np.ndarray | None) -> None:
@@ -274,6 +280,10 @@ class Reconstruction:
 
     def iterate(self, a: float, b: float, c: float, n: int = 1) -> None:
         ptycho_iterate(self.h, a, b, c, n)
+
+    def sp_iterate(self, lam: float = 1.0, n: int = 1, order=None) -> None:
+        """n passes of sequential projections (order: a permutation, or ascending)."""
+        ptycho_sp_iterate(self.h, lam, order, n)
 
     def run(self, name: str, n: int) -> None:
         self.iterate(*PRESETS[name], n)
