@@ -48,11 +48,13 @@ __device__ __forceinline__ double block_max_double(double v, double* scratch) {
 }
 
 // Object numerator/denominator by position-tiled gather.  One CTA per
-// kObjTileR x 32 object tile; thread (ty, tx) owns pixels (ty + 8 k, tx)
-// (one pixel per thread with 8-row tiles).
+// kObjTileR x 32 object tile walks its list of overlapping windows (each entry
+// carries the position index and the window corner, so one load per window);
+// thread (ty, tx) owns pixels (ty + 8 k, tx) (one pixel per thread with
+// 8-row tiles).
 __global__ void __launch_bounds__(kT) concur_object_kernel(
-    const float2* __restrict__ y, const float2* __restrict__ P, const int2* __restrict__ pos,
-    const int* __restrict__ tile_ptr, const int* __restrict__ tile_list, int N, int Mr, int Mc,
+    const float2* __restrict__ y, const float2* __restrict__ P, const int4* __restrict__ tile_win,
+    const int* __restrict__ tile_ptr, int N, int Mr, int Mc,
     int tiles_c, float2* __restrict__ numO, float* __restrict__ denO, unsigned* __restrict__ maxO) {
     constexpr int KP = kObjTileR / 8;  // pixels per thread
     __shared__ float scratch[kT / 32];
@@ -73,14 +75,13 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
     // deep unrolling keeps several windows' loads in flight per thread
 #pragma unroll (8 / KP)
     for (int l = l0; l < l1; ++l) {
-        const int j = tile_list[l];
-        const int2 s = pos[j];
-        const int cc = mc - s.y;
+        const int4 w = __ldg(tile_win + l);  // (position j, row, col) of the window
+        const int cc = mc - w.z;
         const bool cin = (unsigned)cc < (unsigned)N;
-        const float2* yj = y + (size_t)j * NN;
+        const float2* yj = y + (size_t)w.x * NN;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            const int rr = mr0 + 8 * k - s.x;
+            const int rr = mr0 + 8 * k - w.y;
             if (cin && (unsigned)rr < (unsigned)N) {
                 const int o = rr * N + cc;
                 const float2 pv = __ldg(P + o);
@@ -294,7 +295,7 @@ cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos
     const int NN = N * N;
     if (concur_mode == 0) {
         concur_object_kernel<<<cb.tiles_r * cb.tiles_c, kT, 0, st>>>(
-            y, P, pos, cb.tile_ptr, cb.tile_list, N, Mr, Mc, cb.tiles_c, cb.numO, cb.denO, cb.maxO);
+            y, P, cb.tile_win, cb.tile_ptr, N, Mr, Mc, cb.tiles_c, cb.numO, cb.denO, cb.maxO);
     } else {
         cudaMemsetAsync(cb.numO, 0, M * sizeof(float2), st);
         cudaMemsetAsync(cb.denO, 0, M * sizeof(float), st);

@@ -60,7 +60,7 @@ struct ConcurBufs {
     double* denP;          // [N*N]
     unsigned long long* maxP;  // bits of max(denP) (double, >= 0)
     int* tile_ptr;         // [tiles + 1] CSR of positions overlapping each object tile
-    int* tile_list;
+    int4* tile_win;        // CSR entries (position j, window row, window col, 0)
     int tiles_r, tiles_c, chunks;
 };
 constexpr int kObjTileR = 8;   // object tile rows of the gather

@@ -266,7 +266,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += M * (sizeof(float2) + sizeof(float)) + 16;
     b += chunks * NN * (sizeof(float2) + sizeof(float));
     b += NN * (sizeof(double2) + sizeof(double));
-    b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * tr_per * sizeof(int);
+    b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * (N / kObjTile + 1) * sizeof(int4);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
     b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
     if (precision == PTYCHO_PREC_BF16X3) {
@@ -322,14 +322,14 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
                 tile_cnt[(size_t)ti * tiles_c + tj + 1]++;
     }
     for (size_t t = 1; t < tile_cnt.size(); ++t) tile_cnt[t] += tile_cnt[t - 1];
-    std::vector<int> tile_list((size_t)tile_cnt.back());
+    std::vector<int4> tile_list((size_t)tile_cnt.back());
     {
         std::vector<int> fill(tile_cnt.begin(), tile_cnt.end() - 1);
         for (int j = 0; j < J; ++j) {
             const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
             for (int ti = r / kObjTileR; ti <= (r + N - 1) / kObjTileR; ++ti)
                 for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
-                    tile_list[(size_t)fill[(size_t)ti * tiles_c + tj]++] = j;
+                    tile_list[(size_t)fill[(size_t)ti * tiles_c + tj]++] = make_int4(j, r, c, 0);
         }
     }
 
@@ -374,7 +374,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.denP, NN);
     PT_ALLOC(ctx->cb.maxP, (size_t)1);
     PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
-    PT_ALLOC(ctx->cb.tile_list, tile_list.size() > 0 ? tile_list.size() : 1);
+    PT_ALLOC(ctx->cb.tile_win, tile_list.size() > 0 ? tile_list.size() : 1);
     PT_ALLOC(psum, (size_t)J * sq_blocks);
     double* psum_t = nullptr;
     if (tc) {
@@ -422,7 +422,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_STEP(cudaMemcpyAsync(ctx->cb.tile_ptr, tile_cnt.data(), tile_cnt.size() * sizeof(int),
                             cudaMemcpyHostToDevice, st));
     if (!tile_list.empty())
-        PT_STEP(cudaMemcpyAsync(ctx->cb.tile_list, tile_list.data(), tile_list.size() * sizeof(int),
+        PT_STEP(cudaMemcpyAsync(ctx->cb.tile_win, tile_list.data(), tile_list.size() * sizeof(int4),
                                 cudaMemcpyHostToDevice, st));
     PT_STEP(cudaMemsetAsync(ctx->dflag, 0, 4 * sizeof(int), st));
     PT_STEP(cudaMemsetAsync(ctx->d_iter, 0, sizeof(unsigned long long), st));
