@@ -201,6 +201,15 @@ int ptycho_probe_update_noalloc(const float* y, const float* obj, const int32_t*
                                 int32_t J, int32_t N, int32_t M_rows, int32_t M_cols,
                                 float alpha, float* probe_out, void* stream);
 
+/* Diagnostic of the failure handling (no counterpart in the paper): every
+ * wait inside the library's kernels is bounded in time and reports expiry to
+ * the host instead of hanging the device.  This runs such a wait on device
+ * `device` on a flag that nothing sets, bounded by timeout_ms (1..10000);
+ * the expected result is PTYCHO_ETIMEOUT, after which the device and every
+ * context on it remain usable.  Synchronises the device.
+ * Errors: EINVAL (bad device or timeout), ECUDA. */
+int ptycho_check_bounded_wait(int device, uint32_t timeout_ms);
+
 /* Bytes of device memory the context holds for its current scan. */
 size_t ptycho_device_bytes(const ptycho_ctx* ctx);
 

@@ -22,13 +22,16 @@
 // re-split of the previous iteration, exactly as the FP32 kernel does) and
 // writes its hi/lo planes.
 //
-// GEMM kernel: persistent, one CTA per SM looping over 128 x 256 output tiles
-// (128 rows x 128 complex columns of one exit wave); warp 0 issues TMA loads
-// (128-byte swizzle) into a 4-stage shared-memory ring that runs on across
-// tiles, warp 1 allocates all 512 tensor-memory columns (two accumulators)
-// and issues tcgen05.mma (M = 128, N = 256, K = 16) from one thread, warps
-// 2-5 drain one accumulator with tcgen05.ld and run the epilogue while the
-// MMAs of the next tile fill the other.  Every wait
+// GEMM kernel: persistent, one CTA per SM, in clusters of two; each pair
+// works on two 128 x 256 output tiles (128 rows x 128 complex columns) that
+// share the same B tile: each CTA loads its own A tile and one half of the B
+// tile, multicast into both CTAs' shared memory (the MMA commits are
+// multicast too, so a stage is refilled only when both CTAs are done with
+// it).  Warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring that
+// runs on across tiles, warp 1 allocates all 512 tensor-memory columns (two
+// accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16) from one
+// thread, warps 2-5 drain one accumulator with tcgen05.ld and run the
+// epilogue while the MMAs of the next tile fill the other.  Every wait
 // on an mbarrier is bounded in time; on expiry the kernel records an error
 // flag, drains and returns (the host reports PTYCHO_ETIMEOUT).
 #include <cuda.h>
@@ -121,6 +124,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
+// The same load into this CTA and its cluster partner (same shared-memory
+// offset and mbarrier offset in both), for operand halves shared by a pair.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                               uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar), "h"(mask)
+        : "memory");
+}
+// Arrive on the mbarrier at this offset in every CTA of the mask once the
+// issued MMAs complete.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -180,11 +203,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
 
+    // CTA pairs (clusters of 2) take the two row blocks 2 p and 2 p + 1 of one
+    // output column block: each loads its A tile and one half of the shared B
+    // tile, multicast to both.
+    unsigned int rank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    const uint16_t pair_mask = 0x3;
+
     const int N = g.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt_per = N / kBM, nt_per = (2 * N) / kBN;
-    const int tiles_per = mt_per * nt_per;
-    const int tiles = g.J * tiles_per;
+    const int row_blocks = g.J * mt_per;                 // 128-row blocks over all exit waves
+    const int pairs = ((row_blocks + 1) / 2) * nt_per;   // work items of a CTA pair
+    const int pair0 = blockIdx.x / 2, pair_step = gridDim.x / 2;
     const int KBP = (2 * N) / kBK;      // k-blocks per product
     const int KB = 3 * KBP;             // hi*hi, hi*lo, lo*hi
 
@@ -193,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 2);   // the MMAs of both CTAs of the pair
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(afull0 + 8 * b, 1);   // one tcgen05.commit
@@ -209,18 +240,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    // both CTAs' barriers are initialised before any multicast can reach them
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer: the stage ring runs on across tiles
+        // producer: the stage ring runs on across work items
         uint32_t gk = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            const int j = t / tiles_per, t_in = t % tiles_per;
-            const int mt = t_in / nt_per, nt = t_in % nt_per;
-            const int row0 = j * N + mt * kBM;
+        for (int q = pair0; q < pairs && ok; q += pair_step) {
+            const int rb = 2 * (q / nt_per) + (int)rank, nt = q % nt_per;
+            const int row0 = rb * kBM;   // beyond the last block: TMA fills zeros
             for (int kb = 0; kb < KB; ++kb, ++gk) {
                 const uint32_t s = gk % kStages, ph = (gk / kStages) & 1u;
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, g.err_flag)) {
@@ -230,15 +261,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(full0 + 8 * s, kABytes + kBBytes);
                 const int pair = kb / KBP, kin = (kb % KBP) * kBK;
                 tma_load_2d(sA + s * kABytes, pair == 2 ? &mapAlo : &mapAhi, kin, row0, full0 + 8 * s);
-                tma_load_2d(sB + s * kBBytes, pair == 1 ? &mapBlo : &mapBhi, kin, nt * kBN, full0 + 8 * s);
+                tma_load_2d_mc(sB + s * kBBytes + rank * (kBBytes / 2), pair == 1 ? &mapBlo : &mapBhi,
+                               kin, nt * kBN + (int)rank * (kBN / 2), full0 + 8 * s, pair_mask);
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: accumulator i & 1 of the i-th tile of this CTA
+        // MMA issuer: accumulator i & 1 of the i-th work item of this CTA
         uint32_t gk = 0;
         bool ok = true;
         int i = 0;
-        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        for (int q = pair0; q < pairs && ok; q += pair_step, ++i) {
             const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
             if (!mbar_wait(aempty0 + 8 * ab, aph ^ 1u, g.err_flag)) break;  // epilogue done with it
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -256,29 +288,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bd = desc_sw128(sB + s * kBBytes + kk * 32);
                     mma_bf16(acc, ad, bd, (kb | kk) != 0 ? 1u : 0u);
                 }
-                mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs complete
+                // the stage is free in both CTAs once these MMAs complete
+                mma_commit_mc(empty0 + 8 * s, pair_mask);
             }
             mma_commit(afull0 + 8 * ab);     // the accumulator is complete
         }
     } else if (warp >= 2) {
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
-        const int q = warp & 3;
+        const int qw = warp & 3;
         const size_t NN = (size_t)N * N;
         const float inv_n2 = 1.0f / (float)(N * N);
         const float cr = g.c, oc = 1.0f - g.c;
         int i = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
-            const int j = t / tiles_per, t_in = t % tiles_per;
-            const int mt = t_in / nt_per, nt = t_in % nt_per;
-            const int m = mt * kBM + 32 * q + lane;  // row within the exit wave
+        for (int q = pair0; q < pairs; q += pair_step, ++i) {
+            const int rb = 2 * (q / nt_per) + (int)rank, nt = q % nt_per;
+            const int j = rb / mt_per, mt = rb % mt_per;
+            const bool real = rb < row_blocks;
+            const int m = mt * kBM + 32 * qw + lane;  // row within the exit wave
             const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
             if (!mbar_wait(afull0 + 8 * ab, aph, g.err_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float err = 0.f;
 #pragma unroll 1
-            for (int ch = 0; ch < kBN / 32; ++ch) {
+            for (int ch = 0; ch < kBN / 32 && real; ++ch) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ab * kTmemCols + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * ch), r);
+                tmem_ld32(tmem + ab * kTmemCols + ((uint32_t)(32 * qw) << 16) + (uint32_t)(32 * ch), r);
                 const int v0 = nt * (kBN / 2) + 16 * ch;  // first complex column of the chunk
                 if constexpr (EPI == kEpiSplitT) {
                     // next operand row v, column m (re) and N + m (im)
@@ -344,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float e = err;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-                if (lane == 0) g.e_part[(size_t)t * 4 + q] = (double)e;
+                if (lane == 0 && real) g.e_part[((size_t)rb * nt_per + nt) * 4 + qw] = (double)e;
             }
         }
     }
@@ -356,6 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(2 * kTmemCols)
                      : "memory");
     }
+    // neither CTA leaves while its partner may still signal its barriers
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // x_k (load or re-split, the same expression as the FP32 divide kernel) and
@@ -523,7 +559,7 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt
     CUtensorMap mA[4], mB[4];
     for (int i = 0; i < 4; ++i) {
         if (!make_map(&mA[i], planes[i], rows, cols, kBM)) return cudaErrorInvalidValue;
-        if (!make_map(&mB[i], B[i], cols, cols, kBN)) return cudaErrorInvalidValue;
+        if (!make_map(&mB[i], B[i], cols, cols, kBN / 2)) return cudaErrorInvalidValue;
     }
     GemmArgs g{};
     g.N = N;
@@ -533,7 +569,8 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt
     g.c = a.c;
     g.err_flag = err_flag;
     g.y = a.y;
-    const int tiles = bf16x3_tiles(N, a.J);
+    const int row_blocks = a.J * (N / kBM);
+    const int pairs = ((row_blocks + 1) / 2) * ((2 * N) / kBN);
     static int n_sm = 0;
     if (n_sm == 0) {
         int dev = 0;
@@ -541,21 +578,38 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
             n_sm = 148;
     }
-    const int grid = tiles < n_sm ? tiles : n_sm;  // persistent: one CTA per SM
+    // persistent: one CTA per SM, in pairs
+    const int grid = 2 * (pairs < n_sm / 2 ? pairs : n_sm / 2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     // 1: Z = X F -> Z^T into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    dft_gemm_kernel<kEpiSplitT><<<grid, kThreads, kSmem, st>>>(mA[0], mA[1], mB[0], mB[1], g);
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[0], mB[1], g)) != cudaSuccess)
+        return e;
     // 2: Psi^T = Z^T F, modulus -> Psi''^T into buffer 0
     g.out_hi = p[0];
     g.out_lo = p[1];
-    dft_gemm_kernel<kEpiModulus><<<grid, kThreads, kSmem, st>>>(mA[2], mA[3], mB[0], mB[1], g);
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiModulus>, mA[2], mA[3], mB[0], mB[1], g)) != cudaSuccess)
+        return e;
     // 3: G^T = Psi''^T conj(F) -> G into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    dft_gemm_kernel<kEpiSplitT><<<grid, kThreads, kSmem, st>>>(mA[0], mA[1], mB[2], mB[3], g);
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[2], mB[3], g)) != cudaSuccess)
+        return e;
     // 4: y = G conj(F)
-    dft_gemm_kernel<kEpiOut><<<grid, kThreads, kSmem, st>>>(mA[2], mA[3], mB[2], mB[3], g);
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiOut>, mA[2], mA[3], mB[2], mB[3], g)) != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 
 #include "../../include/ptycho.h"
 #include "internal.h"
+#include "nvtx.h"
 
 using namespace ptycho;
 
@@ -283,6 +284,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
 int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_rc,
                      const float* intensity, int32_t M_rows, int32_t M_cols, const float* obj0,
                      const float* probe0, uint32_t flags) {
+    NvtxRange nvtx_range("ptycho_load_scan");
     if (!ctx) return PTYCHO_EINVAL;
     ctx->err.clear();
     if (J < 1) return fail(ctx, PTYCHO_EINVAL, "J must be >= 1");
@@ -469,6 +471,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
 }
 
 int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
+    NvtxRange nvtx_range("ptycho_iterate");
     if (!ctx) return PTYCHO_EINVAL;
     ctx->err.clear();
     if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
@@ -610,6 +613,7 @@ int ptycho_errors(ptycho_ctx* ctx, double* fourier_err, int32_t cap, int32_t* n_
 int64_t ptycho_iteration_count(const ptycho_ctx* ctx) { return ctx && ctx->loaded ? ctx->iters : 0; }
 
 int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
+    NvtxRange nvtx_range("ptycho_model_error");
     if (!ctx || !fourier_err) return ctx ? fail(ctx, PTYCHO_EINVAL, "NULL output") : PTYCHO_EINVAL;
     ctx->err.clear();
     if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
@@ -645,6 +649,7 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
 size_t ptycho_device_bytes(const ptycho_ctx* ctx) { return ctx ? ctx->bytes : 0; }
 
 int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t n_iter) {
+    NvtxRange nvtx_range("ptycho_sp_iterate");
     if (!ctx) return PTYCHO_EINVAL;
     ctx->err.clear();
     if (!std::isfinite(lam)) return fail(ctx, PTYCHO_EINVAL, "lam must be finite");

@@ -26,6 +26,7 @@
 #include "../../include/ptycho.h"
 #include "../../include/ptycho_serve.h"
 #include "internal.h"
+#include "nvtx.h"
 
 using Clock = std::chrono::steady_clock;
 
@@ -82,6 +83,7 @@ extern "C" int ptycho_batch_add(ptycho_batch* b, ptycho_ctx* ctx, float a, float
 }
 
 extern "C" int ptycho_batch_run(ptycho_batch* b, int32_t n_iter) {
+    NvtxRange nvtx_range("ptycho_batch_run");
     if (!b || n_iter < 0) return PTYCHO_EINVAL;
     if (b->e.empty()) return PTYCHO_ESTATE;
     if (n_iter == 0) return PTYCHO_OK;
@@ -258,6 +260,7 @@ void retire(ptycho_server* s, Request* r) {
 
 extern "C" int ptycho_server_step(ptycho_server* s, int32_t iters_per_round, int32_t* n_active,
                                   int32_t* n_queued) {
+    NvtxRange nvtx_range("ptycho_server_step");
     if (!s || iters_per_round < 1) return PTYCHO_EINVAL;
     int prev = 0;
     cudaGetDevice(&prev);

@@ -70,6 +70,7 @@ _SIGS = {
                                         ctypes.c_int32, _P, _P, ctypes.c_uint32]),
     "ptycho_iterate": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int32]),
     "ptycho_sp_iterate": (ctypes.c_int, [_P, ctypes.c_float, _P, ctypes.c_int32]),
+    "ptycho_check_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32]),
     "ptycho_get_object_probe": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_set_object_probe": (ctypes.c_int, [_P, _P, _P]),
     "ptycho_get_exit_waves": (ctypes.c_int, [_P, _P]),
@@ -171,6 +172,11 @@ def ptycho_load_scan(h, pos, intensity, obj0, probe0) -> None:
 
 def ptycho_iterate(h, a: float, b: float, c: float, n_iter: int) -> None:
     _check(lib().ptycho_iterate(h, a, b, c, n_iter), h)
+
+
+def ptycho_check_bounded_wait(device: int, timeout_ms: int) -> int:
+    """Status code of a bounded wait that must expire (PTYCHO_ETIMEOUT expected)."""
+    return int(lib().ptycho_check_bounded_wait(device, timeout_ms))
 
 
 def ptycho_sp_iterate(h, lam: float, order, n_iter: int) -> None:

@@ -71,6 +71,22 @@ def test_iterations_track_the_fp32_path(scan):
     assert rel_l2(O16, O32) <= TOL
 
 
+def test_odd_row_block_count():
+    """J = 9 waves of 128 x 128: an odd number of 128-row blocks, so one CTA
+    pair of the GEMM has a block beyond the last wave (loaded as zeros, no
+    output)."""
+    sc = synth.make_scan(small_spec(128, 3, 3, seed=77, photons=1e6))
+    assert sc.J == 9
+    prob, x0 = oracle_problem(sc)
+    y_ref = oabc.relax(prob.project_D, 2.0)(x0)
+    with gpu_recon(sc, precision="bf16x3") as r:
+        r.iterate(1.0, 0.0, 2.0, 1)
+        y = r.exit_waves()
+        e = r.errors()
+    assert rel_l2(y, y_ref) <= 1e-4
+    assert abs(e[0] - prob.last_error) <= TOL * prob.last_error
+
+
 def test_bf16x3_rejects_other_sizes():
     sc = synth.make_scan(small_spec(64, 2, 2, seed=3))
     with native.Reconstruction(precision="bf16x3") as r:
