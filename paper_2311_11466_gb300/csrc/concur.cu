@@ -48,19 +48,21 @@ __device__ __forceinline__ double block_max_double(double v, double* scratch) {
 }
 
 // Object numerator/denominator by position-tiled gather.  One CTA per
-// kObjTileR x 32 object tile walks its list of overlapping windows (each entry
-// carries the position index and the window corner, so one load per window);
-// thread (ty, tx) owns pixels (ty + 8 k, tx) (one pixel per thread with
-// 8-row tiles).
+// kObjTileR x kObjTile object tile walks its list of overlapping windows (each
+// entry carries the position index and the window corner, so one load per
+// window); thread i owns column i % kObjTile of rows i / kObjTile + kTRG k.
+constexpr int kTRG = kT / kObjTile;       // rows covered by one sweep of the CTA
+static_assert(kT % kObjTile == 0 && kObjTileR % kTRG == 0, "object tile shape");
+
 __global__ void __launch_bounds__(kT) concur_object_kernel(
     const float2* __restrict__ y, const float2* __restrict__ P, const int4* __restrict__ tile_win,
     const int* __restrict__ tile_ptr, int N, int Mr, int Mc,
     int tiles_c, float2* __restrict__ numO, float* __restrict__ denO, unsigned* __restrict__ maxO) {
-    constexpr int KP = kObjTileR / 8;  // pixels per thread
+    constexpr int KP = kObjTileR / kTRG;  // pixels per thread
     __shared__ float scratch[kT / 32];
     const int tile = blockIdx.x;
     const int ti = tile / tiles_c, tj = tile % tiles_c;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int tx = threadIdx.x % kObjTile, ty = threadIdx.x / kObjTile;
     const int mc = tj * kObjTile + tx;
     const int mr0 = ti * kObjTileR + ty;
     float2 acc[KP];
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
     const size_t NN = (size_t)N * N;
     const int l0 = tile_ptr[tile], l1 = tile_ptr[tile + 1];
     // deep unrolling keeps several windows' loads in flight per thread
-#pragma unroll (8 / KP)
+#pragma unroll(KP >= 8 ? 1 : 8 / KP)
     for (int l = l0; l < l1; ++l) {
         const int4 w = __ldg(tile_win + l);  // (position j, row, col) of the window
         const int cc = mc - w.z;
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
         const float2* yj = y + (size_t)w.x * NN;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            const int rr = mr0 + 8 * k - w.y;
+            const int rr = mr0 + kTRG * k - w.y;
             if (cin && (unsigned)rr < (unsigned)N) {
                 const int o = rr * N + cc;
                 const float2 pv = __ldg(P + o);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kT) concur_object_kernel(
     float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
-        const int mr = mr0 + 8 * k;
+        const int mr = mr0 + kTRG * k;
         if (mr < Mr && mc < Mc) {
             numO[(size_t)mr * Mc + mc] = acc[k];
             denO[(size_t)mr * Mc + mc] = den[k];

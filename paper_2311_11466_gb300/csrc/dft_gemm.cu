@@ -73,7 +73,7 @@ struct GemmArgs {
     __nv_bfloat16* out_hi;  // next A operand planes [J*N][2N]
     __nv_bfloat16* out_lo;
     float2* y;              // final output [J][N][N]
-    const float* sqrtIt;    // [J][N][N] sqrt(I) transposed: [j][v][u]
+    const float* sqrtI;     // [J][N][N] sqrt(I), the patterns' own layout [j][u][v]
     double* e_part;         // [tiles] error partials
     float c;                // divide relaxation
     int* err_flag;
@@ -329,13 +329,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         g.out_lo[o + N] = l;
                     }
                 } else if constexpr (EPI == kEpiModulus) {
-                    // rows are column frequencies v = m, columns row frequencies u
-                    const float* sq = g.sqrtIt + (size_t)j * NN + (size_t)m * N + v0;
+                    // rows are column frequencies v = m, columns row frequencies
+                    // u = v0 + ii: sqrt(I)[u][m], one 128-byte line per warp and ii
+                    const float* sq = g.sqrtI + (size_t)j * NN + (size_t)v0 * N + m;
                     alignas(16) __nv_bfloat16 hr[16], hi_[16], lr[16], li[16];
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) {
                         const float re = __uint_as_float(r[2 * ii]), im = __uint_as_float(r[2 * ii + 1]);
-                        const float sv = __ldg(sq + ii);
+                        const float sv = __ldg(sq + (size_t)ii * N);
                         const float m2 = fmaf(re, re, im * im);
                         const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
                         const float d = fmaf(m2, rs, -sv);
@@ -426,13 +427,12 @@ __global__ void __launch_bounds__(256) bf16_prologue_kernel(
     alo[o + N] = l;
 }
 
-// sqrt(I) transposed: out[j][v][u] = sqrt(I[j][u][v]); flags bad values and
-// writes FP64 partial sums of I per (pattern, tile).
-__global__ void __launch_bounds__(256) sqrt_transpose_kernel(const float* __restrict__ I,
+// sqrt(I) in the patterns' own layout; flags bad values and writes FP64
+// partial sums of I per (pattern, 32 x 32 tile).
+__global__ void __launch_bounds__(256) sqrt_intensity_kernel(const float* __restrict__ I,
                                                              float* __restrict__ out, int N,
                                                              double* __restrict__ psum,
                                                              int* __restrict__ bad) {
-    __shared__ float t[32][33];
     __shared__ double red[8];
     const int j = blockIdx.z;
     const int u0 = blockIdx.y * 32, v0 = blockIdx.x * 32;
@@ -440,13 +440,12 @@ __global__ void __launch_bounds__(256) sqrt_transpose_kernel(const float* __rest
     const size_t base = (size_t)j * N * N;
     double s = 0.0;
     for (int k = ty; k < 32; k += 8) {
-        const float val = I[base + (size_t)(u0 + k) * N + v0 + tx];
+        const size_t o = base + (size_t)(u0 + k) * N + v0 + tx;
+        const float val = I[o];
         if (!(val >= 0.0f) || !isfinite(val)) atomicOr(bad, 1);
         s += (double)val;
-        t[k][tx] = sqrtf(fmaxf(val, 0.0f));
+        out[o] = sqrtf(fmaxf(val, 0.0f));
     }
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) out[base + (size_t)(v0 + k) * N + u0 + tx] = t[tx][k];
     const double tot = block_sum_double<256>(s, red);
     if (threadIdx.x == 0)
         psum[((size_t)j * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
@@ -538,16 +537,16 @@ cudaError_t bf16x3_prepare() {
                                 (int)kSmem);
 }
 
-cudaError_t launch_sqrt_transpose(int N, const float* I, float* out, double* psum, int* bad, int J,
+cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, double* psum, int* bad, int J,
                                   cudaStream_t st) {
     dim3 grid(N / 32, N / 32, J);
-    sqrt_transpose_kernel<<<grid, 256, 0, st>>>(I, out, N, psum, bad);
+    sqrt_intensity_kernel<<<grid, 256, 0, st>>>(I, out, N, psum, bad);
     return cudaGetLastError();
 }
 
 // One divide step on the tensor-core path.  planes: two ping-pong operand
 // buffers, each hi then lo, [J*N][2N] bf16.  B: fwd hi, fwd lo, inv hi, inv lo.
-cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt, uint16_t* const planes[4],
+cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI, uint16_t* const planes[4],
                                  const uint16_t* const B[4], int* err_flag, cudaStream_t st) {
     __nv_bfloat16* p[4];
     for (int i = 0; i < 4; ++i) p[i] = reinterpret_cast<__nv_bfloat16*>(planes[i]);
@@ -564,7 +563,7 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt
     GemmArgs g{};
     g.N = N;
     g.J = a.J;
-    g.sqrtIt = sqrtIt;
+    g.sqrtI = sqrtI;
     g.e_part = a.e_part;
     g.c = a.c;
     g.err_flag = err_flag;

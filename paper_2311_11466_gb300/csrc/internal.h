@@ -63,8 +63,14 @@ struct ConcurBufs {
     int4* tile_win;        // CSR entries (position j, window row, window col, 0)
     int tiles_r, tiles_c, chunks;
 };
-constexpr int kObjTileR = 8;   // object tile rows of the gather
-constexpr int kObjTile = 32;   // object tile columns (one warp of pixels)
+#ifndef PTYCHO_OBJ_TILE_R
+#define PTYCHO_OBJ_TILE_R 16
+#endif
+#ifndef PTYCHO_OBJ_TILE_C
+#define PTYCHO_OBJ_TILE_C 32
+#endif
+constexpr int kObjTileR = PTYCHO_OBJ_TILE_R;  // object tile rows of the gather
+constexpr int kObjTile = PTYCHO_OBJ_TILE_C;   // object tile columns
 int probe_chunks(int J, int N);
 cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
                           const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
@@ -89,9 +95,9 @@ int bf16x3_error_parts(int N, int J);
 void bf16x3_constants(int N, std::vector<uint16_t>& fwd_hi, std::vector<uint16_t>& fwd_lo,
                       std::vector<uint16_t>& inv_hi, std::vector<uint16_t>& inv_lo);
 cudaError_t bf16x3_prepare();
-cudaError_t launch_sqrt_transpose(int N, const float* I, float* out, double* psum, int* bad, int J,
+cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, double* psum, int* bad, int J,
                                   cudaStream_t st);
-cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtIt,
+cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI,
                                  uint16_t* const planes[4], const uint16_t* const B[4],
                                  int* err_flag, cudaStream_t st);
 

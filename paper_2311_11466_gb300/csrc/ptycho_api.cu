@@ -42,11 +42,11 @@ struct ptycho_ctx {
 
     float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
     float* sqrtIp = nullptr;
-    float2* scratch = nullptr;  // divide-kernel transpose slots, one per resident cluster
+    float2* scratch = nullptr;  // divide-kernel transpose scratch, one slot per exit wave
     int n_slots = 0;
-    // tensor-core path: sqrt(I) transposed, two ping-pong operand buffers (hi,
+    // tensor-core path: sqrt(I) in the patterns' layout, two ping-pong operand buffers (hi,
     // lo) and the constant DFT operands (fwd hi, fwd lo, inv hi, inv lo)
-    float* sqrtIt = nullptr;
+    float* sqrtI = nullptr;
     uint16_t* planes[4] = {nullptr, nullptr, nullptr, nullptr};
     uint16_t* Bc[4] = {nullptr, nullptr, nullptr, nullptr};
     int2* pos = nullptr;
@@ -115,7 +115,7 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->sqrtIp = nullptr;
     ctx->scratch = nullptr;
     ctx->n_slots = 0;
-    ctx->sqrtIt = nullptr;
+    ctx->sqrtI = nullptr;
     for (int i = 0; i < 4; ++i) ctx->planes[i] = ctx->Bc[i] = nullptr;
     ctx->pos = nullptr;
     ctx->e_part = ctx->e_ring = ctx->e_tmp = nullptr;
@@ -271,7 +271,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
     b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
     if (precision == PTYCHO_PREC_BF16X3) {
-        b += (size_t)J * NN * sizeof(float);           // sqrt(I) transposed
+        b += (size_t)J * NN * sizeof(float);           // sqrt(I), patterns' layout
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
         b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
         b += (size_t)J * (NN / 1024 + 1) * sizeof(double);
@@ -380,7 +380,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(psum, (size_t)J * sq_blocks);
     double* psum_t = nullptr;
     if (tc) {
-        PT_ALLOC(ctx->sqrtIt, (size_t)J * NN);
+        PT_ALLOC(ctx->sqrtI, (size_t)J * NN);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->Bc[i], 4 * NN);
         PT_ALLOC(psum_t, (size_t)J * (NN / 1024));
@@ -441,7 +441,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_STEP(launch_sqrt_permute(N, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
     if (tc) {
         PT_STEP(bf16x3_prepare());
-        PT_STEP(launch_sqrt_transpose(N, Idev, ctx->sqrtIt, psum_t, ctx->dflag, J, st));
+        PT_STEP(launch_sqrt_intensity(N, Idev, ctx->sqrtI, psum_t, ctx->dflag, J, st));
         std::vector<uint16_t> Bh[4];
         bf16x3_constants(N, Bh[0], Bh[1], Bh[2], Bh[3]);
         for (int i = 0; i < 4; ++i)
@@ -504,7 +504,7 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
         int n_part = ctx->J * ctx->C;
         if (ctx->opts.precision == PTYCHO_PREC_BF16X3) {
-            PT_CUDA(ctx, launch_divide_bf16x3(da, ctx->N, ctx->sqrtIt, ctx->planes, ctx->Bc,
+            PT_CUDA(ctx, launch_divide_bf16x3(da, ctx->N, ctx->sqrtI, ctx->planes, ctx->Bc,
                                               ctx->dflag + 1, ctx->stream));
             n_part = bf16x3_error_parts(ctx->N, ctx->J);
         } else {
