@@ -178,31 +178,52 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         inv_maxO = mo > 0.f ? 1.0f / mo : 0.f;
     }
 
-    // Phase 1: form x_k, row DFT pass 1 (lanes over t).
+    // Phase 1a: form x_k for this CTA's rows, two adjacent elements per lane
+    // (16-byte loads, coalesced; few registers live, so many loads in flight),
+    // into the row buffer at the slot of element n = t + B e.
+    static_assert(N % 2 == 0 && B % 2 == 0, "element pairs");
+#pragma unroll 4
+    for (int i = tid; i < R * N / 2; i += T) {
+        const int row = i / (N / 2), n = 2 * (i % (N / 2));
+        const int r = c * R + row;
+        const size_t idx = pat + (size_t)r * N + n;
+        float2 x0, x1;
+        if (load_x) {
+            const float4 f = __ldcs(reinterpret_cast<const float4*>(args.x + idx));
+            x0 = make_float2(f.x, f.y);
+            x1 = make_float2(f.z, f.w);
+        } else {
+            const float4 pv = __ldg(reinterpret_cast<const float4*>(args.P + r * N + n));
+            const float2* op = Ow + (size_t)r * args.Mc + n;
+            const float2 o0 = __ldg(op), o1 = __ldg(op + 1);
+            const float4 yv = need_y ? __ldcs(reinterpret_cast<const float4*>(args.y + idx))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 xp = need_xp ? __ldcs(reinterpret_cast<const float4*>(args.x + idx))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            x0 = resplit_rn(cmul_rn(make_float2(pv.x, pv.y), o0), make_float2(yv.x, yv.y),
+                            make_float2(xp.x, xp.y), args.pa, args.pb);
+            x1 = resplit_rn(cmul_rn(make_float2(pv.z, pv.w), o1), make_float2(yv.z, yv.w),
+                            make_float2(xp.z, xp.w), args.pa, args.pb);
+            if (write_x) __stcs(reinterpret_cast<float4*>(args.x + idx), make_float4(x0.x, x0.y, x1.x, x1.y));
+        }
+        float2* rb = buf + row * RS;
+        rb[(n / B) * (B + 1) + n % B] = x0;          // n even, B even: n + 1 is
+        rb[(n / B) * (B + 1) + n % B + 1] = x1;      // in the same group of B
+    }
+    __syncthreads();
+
+    // Phase 1b: row DFT pass 1 in place (lanes over t): each thread reads the
+    // A slots of its (row, t) and writes its outputs back to the same slots.
 #pragma unroll 1
     for (int task = tid; task < R * B; task += T) {
         const int row = task / B, t = task % B;
-        const int r = c * R + row;
+        float2* p = buf + row * RS + t;
         float2 v[A];
 #pragma unroll
-        for (int e = 0; e < A; ++e) {
-            const int n = t + B * e;
-            const size_t idx = pat + (size_t)r * N + n;
-            float2 xv;
-            if (load_x) {
-                xv = __ldcs(args.x + idx);
-            } else {
-                const float2 z = cmul_rn(__ldg(args.P + r * N + n), __ldg(Ow + (size_t)r * args.Mc + n));
-                const float2 yv = need_y ? __ldcs(args.y + idx) : make_float2(0.f, 0.f);
-                const float2 xp = need_xp ? __ldcs(args.x + idx) : make_float2(0.f, 0.f);
-                xv = resplit_rn(z, yv, xp, args.pa, args.pb);
-                if (write_x) __stcs(args.x + idx, xv);
-            }
-            v[e] = xv;
-        }
+        for (int e = 0; e < A; ++e) v[e] = p[e * (B + 1)];
         dft_reg<A, false>(v);
 #pragma unroll
-        for (int k = 0; k < A; ++k) buf[row * RS + k * (B + 1) + t] = cmul(v[k], twA[k * B + t]);
+        for (int k = 0; k < A; ++k) p[k * (B + 1)] = cmul(v[k], twA[k * B + t]);
     }
     __syncthreads();
 
@@ -451,13 +472,18 @@ cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     cfg.blockDim = dim3(G::T);
     cfg.dynamicSmemBytes = G::SMEM;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = G::C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // Load-balanced placement: with the default (spread: the CTAs of a cluster
+    // on distinct SMs) clusters of 16 never land on 16 of the 152 SMs; with
+    // load balancing every SM takes CTAs (measured 0.907 -> 0.858 ms, large).
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if (a.sp) {
         cfg.gridDim = dim3((unsigned)G::C);  // one cluster: one position
         return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeSP>, a);
@@ -532,13 +558,15 @@ int slots_t() {
     cfg.gridDim = dim3(G::C * 1024);
     cfg.blockDim = dim3(G::T);
     cfg.dynamicSmemBytes = G::SMEM;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = G::C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, divide_kernel<N, kModeDivide>, &cfg) != cudaSuccess || n <= 0) {
         cudaGetLastError();

@@ -40,7 +40,7 @@ int divide_cluster_size(int N);
 void divide_twiddles(int N, std::vector<float2>& tw);
 cudaError_t divide_prepare(int N);  // one-time kernel attributes
 // Clusters of the divide kernel that fit on the device at once (after
-// divide_prepare); the kernel runs that many persistent clusters.
+// divide_prepare): the number of exit waves in flight.
 int divide_slots(int N);
 cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st);
 // sqrt of the intensities into the divide kernel's frequency order; flags
