@@ -299,6 +299,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const size_t NN = (size_t)N * N;
         const float inv_n2 = 1.0f / (float)(N * N);
         const float cr = g.c, oc = 1.0f - g.c;
+        // The modulus epilogue's sqrt(I) block of a work item: rows u of the
+        // item's 128 complex columns, 128 floats (its 128 rows m) each; epilogue
+        // thread e prefetches row e into L2 (512 bytes, 16-byte aligned).
+        auto prefetch_sqrt = [&](int qq) {
+            if constexpr (EPI == kEpiModulus) {
+                const int rb2 = 2 * (qq / nt_per) + (int)rank, nt2 = qq % nt_per;
+                if (qq < pairs && rb2 < row_blocks) {
+                    const int e = 32 * qw + lane;
+                    const float* src = g.sqrtI + (size_t)(rb2 / mt_per) * NN +
+                                       (size_t)(nt2 * (kBN / 2) + e) * N + (rb2 % mt_per) * kBM;
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(kBM * 4)
+                                 : "memory");
+                }
+            }
+        };
+        prefetch_sqrt(pair0);
         int i = 0;
         for (int q = pair0; q < pairs; q += pair_step, ++i) {
             const int rb = 2 * (q / nt_per) + (int)rank, nt = q % nt_per;
@@ -308,7 +324,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
             if (!mbar_wait(afull0 + 8 * ab, aph, g.err_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            prefetch_sqrt(q + pair_step);  // the next item's, while this one drains
             float err = 0.f;
+            // sqrt(I) of chunk ch + 1 is loaded while chunk ch is processed
+            float sv_next[16];
+            if constexpr (EPI == kEpiModulus) {
+                if (real) {
+                    const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(nt * (kBN / 2)) * N + m;
+#pragma unroll
+                    for (int ii = 0; ii < 16; ++ii) sv_next[ii] = __ldg(sq + (size_t)ii * N);
+                }
+            }
 #pragma unroll 1
             for (int ch = 0; ch < kBN / 32 && real; ++ch) {
                 uint32_t r[32];
@@ -331,12 +357,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if constexpr (EPI == kEpiModulus) {
                     // rows are column frequencies v = m, columns row frequencies
                     // u = v0 + ii: sqrt(I)[u][m], one 128-byte line per warp and ii
-                    const float* sq = g.sqrtI + (size_t)j * NN + (size_t)v0 * N + m;
+                    float svc[16];
+#pragma unroll
+                    for (int ii = 0; ii < 16; ++ii) svc[ii] = sv_next[ii];
+                    if (ch + 1 < kBN / 32) {
+                        const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(v0 + 16) * N + m;
+#pragma unroll
+                        for (int ii = 0; ii < 16; ++ii) sv_next[ii] = __ldg(sq + (size_t)ii * N);
+                    }
                     alignas(16) __nv_bfloat16 hr[16], hi_[16], lr[16], li[16];
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) {
                         const float re = __uint_as_float(r[2 * ii]), im = __uint_as_float(r[2 * ii + 1]);
-                        const float sv = __ldg(sq + (size_t)ii * N);
+                        const float sv = svc[ii];
                         const float m2 = fmaf(re, re, im * im);
                         const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
                         const float d = fmaf(m2, rs, -sv);
