@@ -30,7 +30,8 @@
 // it).  Warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring that
 // runs on across tiles, warp 1 allocates all 512 tensor-memory columns (two
 // accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16) from one
-// thread, warps 2-5 drain one accumulator with tcgen05.ld and run the
+// thread, warps 2-9 (two per tensor-memory lane quarter, even and odd
+// column chunks) drain one accumulator with tcgen05.ld and run the
 // epilogue while the MMAs of the next tile fill the other.  Every wait
 // on an mbarrier is bounded in time; on expiry the kernel records an error
 // flag, drains and returns (the host reports PTYCHO_ETIMEOUT).
@@ -52,7 +53,8 @@ constexpr int kBM = 128;         // tile rows (MMA M)
 constexpr int kBN = 256;         // tile columns (MMA N) = 128 complex outputs
 constexpr int kBK = 64;          // K per pipeline stage (128 bytes of bf16)
 constexpr int kStages = 4;
-constexpr int kThreads = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;     // two per tensor-memory lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KiB
 constexpr uint32_t kBBytes = kBN * kBK * 2;  // 32 KiB
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(afull0 + 8 * b, 1);   // one tcgen05.commit
-            mbar_init(aempty0 + 8 * b, 4);  // one arrival per epilogue warp
+            mbar_init(aempty0 + 8 * b, kEpiWarps);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -294,22 +296,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(afull0 + 8 * ab);     // the accumulator is complete
         }
     } else if (warp >= 2) {
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
-        const int qw = warp & 3;
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the
+        // even (half 0) or odd (half 1) 32-column chunks
+        const int qw = warp & 3, half = (warp - 2) / 4;
         const size_t NN = (size_t)N * N;
         const float inv_n2 = 1.0f / (float)(N * N);
         const float cr = g.c, oc = 1.0f - g.c;
         // The modulus epilogue's sqrt(I) block of a work item: rows u of the
         // item's 128 complex columns, 128 floats (its 128 rows m) each; epilogue
-        // thread e prefetches row e into L2 (512 bytes, 16-byte aligned).
+        // thread e of each half prefetches that half of row e into L2 (256
+        // bytes, 16-byte aligned).
         auto prefetch_sqrt = [&](int qq) {
             if constexpr (EPI == kEpiModulus) {
                 const int rb2 = 2 * (qq / nt_per) + (int)rank, nt2 = qq % nt_per;
                 if (qq < pairs && rb2 < row_blocks) {
                     const int e = 32 * qw + lane;
                     const float* src = g.sqrtI + (size_t)(rb2 / mt_per) * NN +
-                                       (size_t)(nt2 * (kBN / 2) + e) * N + (rb2 % mt_per) * kBM;
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(kBM * 4)
+                                       (size_t)(nt2 * (kBN / 2) + e) * N + (rb2 % mt_per) * kBM +
+                                       half * (kBM / 2);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(kBM * 2)
                                  : "memory");
                 }
             }
@@ -326,17 +331,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             prefetch_sqrt(q + pair_step);  // the next item's, while this one drains
             float err = 0.f;
-            // sqrt(I) of chunk ch + 1 is loaded while chunk ch is processed
+            // sqrt(I) of a warp's next chunk is loaded while the current one is processed
             float sv_next[16];
             if constexpr (EPI == kEpiModulus) {
                 if (real) {
-                    const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(nt * (kBN / 2)) * N + m;
+                    const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(nt * (kBN / 2) + 16 * half) * N + m;
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) sv_next[ii] = __ldg(sq + (size_t)ii * N);
                 }
             }
 #pragma unroll 1
-            for (int ch = 0; ch < kBN / 32 && real; ++ch) {
+            for (int ch = half; ch < kBN / 32 && real; ch += 2) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ab * kTmemCols + ((uint32_t)(32 * qw) << 16) + (uint32_t)(32 * ch), r);
                 const int v0 = nt * (kBN / 2) + 16 * ch;  // first complex column of the chunk
@@ -360,8 +365,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float svc[16];
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) svc[ii] = sv_next[ii];
-                    if (ch + 1 < kBN / 32) {
-                        const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(v0 + 16) * N + m;
+                    if (ch + 2 < kBN / 32) {
+                        const float* sq = g.sqrtI + (size_t)j * NN + (size_t)(v0 + 32) * N + m;
 #pragma unroll
                         for (int ii = 0; ii < 16; ++ii) sv_next[ii] = __ldg(sq + (size_t)ii * N);
                     }
@@ -412,7 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float e = err;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-                if (lane == 0 && real) g.e_part[((size_t)rb * nt_per + nt) * 4 + qw] = (double)e;
+                if (lane == 0 && real)
+                    g.e_part[((size_t)rb * nt_per + nt) * kEpiWarps + 4 * half + qw] = (double)e;
             }
         }
     }
@@ -520,7 +526,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, ui
 bool bf16x3_supported(int N) { return N == 128 || N == 256; }
 
 int bf16x3_tiles(int N, int J) { return J * (N / kBM) * ((2 * N) / kBN); }
-int bf16x3_error_parts(int N, int J) { return 4 * bf16x3_tiles(N, J); }  // one per epilogue warp and tile
+int bf16x3_error_parts(int N, int J) { return kEpiWarps * bf16x3_tiles(N, J); }  // one per epilogue warp and tile
 
 // The constant B operands (K-major, output columns interleaved re/im), hi and
 // lo parts: fwd for F, inv for conj(F).  Layout [2N rows (output)][2N (k)].

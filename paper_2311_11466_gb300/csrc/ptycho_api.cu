@@ -275,8 +275,8 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
         b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
         b += (size_t)J * (NN / 1024 + 1) * sizeof(double);
-        const size_t tiles = 4 * (size_t)J * (N / 128 > 0 ? (N / 128) * (N / 128) : 1);
-        if (tiles > (size_t)J * C) b += (tiles - (size_t)J * C) * sizeof(double);
+        const size_t parts = (size_t)bf16x3_error_parts(N, J);  // a second, larger error buffer
+        if (parts > (size_t)J * C) b += parts * sizeof(double);
     }
     return b;
 }
