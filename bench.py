@@ -179,6 +179,85 @@ def oracle_rate(scan, side: int, min_seconds: float, max_iters: int):
     return len(idx) * len(times) / sum(times), len(times), len(idx)
 
 
+def _oracle_one_thread(scan, side: int, seconds: float):
+    """The same oracle timing with one BLAS/OpenMP thread, in a child process
+    (the thread count of numpy's BLAS is fixed when numpy loads)."""
+    import numpy as np
+    idx = _sub_scan(scan, side)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sample.npz")
+        np.savez(path, intensity=scan.intensity[idx], pos=scan.pos[idx], obj0=scan.obj0,
+                 probe0=scan.probe0)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = "1"
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench._oracle_sample_rate(%r, %r)))" % (ROOT, path, seconds))
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600)
+    if out.returncode != 0:
+        return None
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def _oracle_sample_rate(path: str, seconds: float):
+    import numpy as np
+    from oracle import ptycho as optycho
+    d = np.load(path)
+    prob = optycho.Problem(d["intensity"].astype(np.float64), d["pos"],
+                           d["obj0"].astype(np.complex128), d["probe0"].astype(np.complex128))
+    x = optycho.exit_waves(prob.P, prob.O, d["pos"])
+    times = []
+    t_all = time.perf_counter()
+    while time.perf_counter() - t_all < seconds or not times:
+        t0 = time.perf_counter()
+        x = prob.iterate(x, *RAAR)
+        times.append(time.perf_counter() - t0)
+    return {"value": len(d["pos"]) * len(times) / sum(times), "iterations": len(times)}
+
+
+def cufft_divide_ms(scan, c: float, device, reps: int = 10):
+    """For comparison only (not the library's path): the same divide step as
+    separate library calls (torch.fft, i.e. cuFFT, plus elementwise kernels)
+    on the same workload -- forward 2-D FFT, modulus projection with the c
+    relaxation, inverse 2-D FFT, and the Fourier-error sum -- and the two
+    FFTs alone.  The fused kernel also forms x_k (the re-split), which these
+    sequences leave out.  Returns (whole sequence ms, FFTs only ms)."""
+    import torch
+    J, N = scan.J, scan.N
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.complex(torch.randn(J, N, N, generator=g), torch.randn(J, N, N, generator=g)).to(device)
+    sq = torch.from_numpy(scan.intensity).to(device).sqrt_()
+    st = torch.cuda.Stream(device=device)
+
+    def step():
+        Psi = torch.fft.fft2(x)
+        a = Psi.abs()
+        err = ((a - sq) ** 2).sum(dtype=torch.float64)
+        Psi2 = torch.where(a > 0, (c * sq / a + (1.0 - c)) * Psi, (c * sq).to(Psi.dtype))
+        return torch.fft.ifft2(Psi2), err
+
+    def ffts_only():
+        return torch.fft.ifft2(torch.fft.fft2(x))
+
+    out = []
+    with torch.cuda.stream(st):
+        for fn in (step, ffts_only):
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1) / reps)
+    del x, sq
+    torch.cuda.empty_cache()
+    return out[0], out[1]
+
+
 def _cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -350,6 +429,7 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the cuFFT comparison timing")
     ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve", "compare"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--preset", default="RAAR", choices=["DC", "AR", "DR", "SF", "RAAR", "RRR"])
@@ -476,12 +556,25 @@ def main():
            "final_fourier_error": final_model_err}
     r.close()
 
+    unfused = None
+    if rank == 0 and args.precision == "fp32" and not args.no_compare:
+        cm, fft_ms = cufft_divide_ms(scan, abc[2], torch.device("cuda", local))
+        unfused = {"divide_ms": cm, "fft2_ifft2_only_ms": fft_ms, "fused_divide_ms": div_avg * 1e3,
+                   "speedup": cm / (div_avg * 1e3),
+                   "kind": "comparison only: torch.fft (cuFFT) fft2 + modulus + ifft2 + error sum "
+                           "on the same workload; the fused kernel also forms x_k"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, npos = oracle_rate(scan, 4, args.cpu_seconds, 1000)
         cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                "sample": f"{npos} positions (4x4 block of the raster, 256^2 patterns, full object), "
                          f"{n} RAAR iterations of the FP64 oracle"}
+        one = _oracle_one_thread(scan, 4, min(args.cpu_seconds, 6.0))
+        if one is not None:
+            cpu["one_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1,
+                                 "sample": f"same sample, {one['iterations']} iterations, "
+                                           f"one BLAS thread"}
 
     if rank == 0:
         line = {
@@ -502,6 +595,8 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if unfused is not None:
+            line["unfused_cufft"] = unfused
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

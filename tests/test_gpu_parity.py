@@ -185,6 +185,43 @@ def test_atomic_concur_within_tolerance(tiny):
     assert rel_l2(O, prob.O) <= TOL
 
 
+def test_zero_exit_waves_take_sqrt_I(tiny):
+    """Where Psi = 0 the modulus projection returns sqrt(I) with phase 0. A zero
+    object makes every exit wave and every Psi zero, so the divide step is
+    y = c F^-1(sqrt I) (a closed form, checked here against numpy's inverse
+    FFT as well) and the Fourier error is exactly 1."""
+    c = 2.0
+    obj0 = np.zeros_like(tiny.obj0)
+    prob = optycho.Problem(tiny.intensity.astype(np.float64), tiny.pos, obj0.astype(np.complex128),
+                           tiny.probe0.astype(np.complex128))
+    x0 = optycho.exit_waves(prob.P, prob.O, tiny.pos)
+    assert not np.any(x0)
+    y_ref = oabc.relax(prob.project_D, c)(x0)
+    closed = c * np.fft.ifft2(np.sqrt(tiny.intensity.astype(np.float64)))
+    assert rel_l2(y_ref, closed) <= 1e-12
+    r = native.Reconstruction()
+    with r:
+        r.load_scan(tiny.pos, tiny.intensity, obj0, tiny.probe0)
+        r.iterate(1.0, 0.0, c, 1)
+        y = r.exit_waves()
+        e = r.errors()
+    assert rel_l2(y, y_ref) <= TOL
+    assert abs(e[0] - 1.0) <= TOL
+
+
+def test_empty_scan_rejected(tiny):
+    N = tiny.N
+    with native.Reconstruction() as r:
+        with pytest.raises(native.PtychoError) as ei:
+            r.load_scan(np.zeros((0, 2), np.int32), np.zeros((0, N, N), np.float32), tiny.obj0,
+                        tiny.probe0)
+        assert ei.value.code == native.PTYCHO_EINVAL
+        # the context stays usable
+        r.load_scan(tiny.pos, tiny.intensity, tiny.obj0, tiny.probe0)
+        r.iterate(*native.PRESETS["DC"], 1)
+        assert r.iteration_count == 1
+
+
 def test_validation_errors(tiny):
     with native.Reconstruction() as r:
         with pytest.raises(native.PtychoError) as ei:
