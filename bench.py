@@ -553,7 +553,17 @@ def main():
            "h2d_bytes_per_step": h2d / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
            "step": f"one reconstruction = load_scan (host, pinned) + {e2e_iters} RAAR iterations "
                    f"+ object/probe/error read-back; bytes per iteration",
-           "final_fourier_error": final_model_err}
+           "final_fourier_error": final_model_err,
+           "fourier_error_iter1": float(errs[0]), f"fourier_error_iter{len(errs)}": float(errs[-1])}
+    if args.precision == "bf16x3" and rank == 0:
+        # the FP32 path on the same scan and iteration count, for the error comparison
+        with native.Reconstruction(device=local, stream=stream.cuda_stream) as r32:
+            r32.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+            r32.iterate(*abc, e2e_iters)
+            e32 = r32.errors()
+            e2e["fp32_same_scan"] = {"fourier_error_iter1": float(e32[0]),
+                                     f"fourier_error_iter{len(e32)}": float(e32[-1]),
+                                     "final_fourier_error": r32.model_error()}
     r.close()
 
     unfused = None
