@@ -425,7 +425,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "precision", "medium", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "medium", "tiny", "large128"])
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

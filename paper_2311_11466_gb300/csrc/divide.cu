@@ -46,7 +46,7 @@ template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 32
 template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64,  RSM = 9, MINB = 4; };
 template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
 template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256, RSM = 9, MINB = 4; };
-template <> struct Cfg<128> { static constexpr int A = 8,  B = 16, C = 4, T = 256, RSM = 9, MINB = 3; };
+template <> struct Cfg<128> { static constexpr int A = 16, B = 8,  C = 8, T = 128, RSM = 9, MINB = 8; };
 template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 16, T = 256, RSM = 1, MINB = 4; };
 
 template <int N>

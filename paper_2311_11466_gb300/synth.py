@@ -205,6 +205,9 @@ NAMED = {
                           radius=64.0, defocus=0.00125, photons=1e6, seed=3),
     "medium": ScanSpec(N=256, ny=16, nx=16, step=32, jitter=4, M_rows=780, M_cols=780,
                        radius=64.0, defocus=0.00125, photons=1e6, seed=5),
+    # the 128^2 half of the uneven-scan mix at the large workload's pixel count
+    "large128": ScanSpec(N=128, ny=64, nx=64, step=16, jitter=2, M_rows=1160, M_cols=1160,
+                         radius=32.0, defocus=0.005, photons=1e6, seed=7),
 }
 
 
