@@ -58,7 +58,9 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;  // warp 0 TMA, warp 1 MMA, warps 
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KiB
 constexpr uint32_t kBBytes = kBN * kBK * 2;  // 32 KiB
-constexpr size_t kSmem = (size_t)kStages * (kABytes + kBBytes) + 1024 /*align*/ + 256;
+constexpr uint32_t kStageBytes = 4096;     // epilogue staging per epilogue warp
+constexpr size_t kSmem = (size_t)kStages * (kABytes + kBBytes) + (size_t)kEpiWarps * kStageBytes +
+                         1024 /*align*/ + 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 // Instruction descriptor of tcgen05.mma.kind::f16: D = F32, A = B = BF16,
@@ -183,6 +185,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // hi = bf16(v), lo = bf16(v - hi), both round to nearest even.
+// Tile store shared -> global through the tensor map (bulk async group of the
+// issuing thread); the source must stay untouched until wait_read.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int c0, int c1, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Generic-proxy shared-memory writes made visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void st_shared_u16(uint32_t a, unsigned short v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
     hi = __float2bfloat16_rn(v);
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
@@ -192,6 +219,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     dft_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
                     const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+                    const __grid_constant__ CUtensorMap mapOhi, const __grid_constant__ CUtensorMap mapOlo,
                     const GemmArgs g) {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
@@ -200,7 +228,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* sm = smem_raw + pad;
     const uint32_t sA = base + pad;                                   // [stages][16 KiB]
     const uint32_t sB = sA + kStages * kABytes;                       // [stages][32 KiB]
-    unsigned char* tail = sm + kStages * (kABytes + kBBytes);
+    const uint32_t sStage = sB + kStages * kBBytes;                   // [epilogue warps][4 KiB]
+    unsigned char* tail = sm + kStages * (kABytes + kBBytes) + kEpiWarps * kStageBytes;
     // full[S], empty[S], acc_full[2], acc_empty[2], then the TMEM address
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
@@ -299,6 +328,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the
         // even (half 0) or odd (half 1) 32-column chunks
         const int qw = warp & 3, half = (warp - 2) / 4;
+        // this warp's staging buffer: each chunk is written here in the output's
+        // layout and leaves by one tensor (TMA) store, so the global writes are
+        // whole lines instead of one 16-byte or 2-byte piece per lane
+        const uint32_t stg = sStage + (uint32_t)(warp - 2) * kStageBytes;
         const size_t NN = (size_t)N * N;
         const float inv_n2 = 1.0f / (float)(N * N);
         const float cr = g.c, oc = 1.0f - g.c;
@@ -325,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int rb = 2 * (q / nt_per) + (int)rank, nt = q % nt_per;
             const int j = rb / mt_per, mt = rb % mt_per;
             const bool real = rb < row_blocks;
-            const int m = mt * kBM + 32 * qw + lane;  // row within the exit wave
+            const int m0 = mt * kBM + 32 * qw;       // first row of this warp's lanes
+            const int m = m0 + lane;                  // row within the exit wave
             const uint32_t ab = (uint32_t)i & 1u, aph = ((uint32_t)i >> 1) & 1u;
             if (!mbar_wait(afull0 + 8 * ab, aph, g.err_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -346,18 +380,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld32(tmem + ab * kTmemCols + ((uint32_t)(32 * qw) << 16) + (uint32_t)(32 * ch), r);
                 const int v0 = nt * (kBN / 2) + 16 * ch;  // first complex column of the chunk
                 if constexpr (EPI == kEpiSplitT) {
-                    // next operand row v, column m (re) and N + m (im)
+                    // next operand rows v0 .. v0 + 15, columns m (re) and N + m (im):
+                    // four [16 v][32 m] bf16 arrays (hi re, hi im, lo re, lo im)
+                    if (lane == 0) bulk_wait_read();  // the previous chunk's store has read the buffer
+                    __syncwarp();
 #pragma unroll
                     for (int ii = 0; ii < 16; ++ii) {
                         const float re = __uint_as_float(r[2 * ii]), im = __uint_as_float(r[2 * ii + 1]);
-                        const size_t o = ((size_t)j * N + v0 + ii) * (2 * N) + m;
                         __nv_bfloat16 h, l;
+                        const uint32_t a = stg + (uint32_t)(ii * 64 + lane * 2);
                         split_bf16(re, h, l);
-                        g.out_hi[o] = h;
-                        g.out_lo[o] = l;
+                        st_shared_u16(a, __bfloat16_as_ushort(h));
+                        st_shared_u16(a + 2048, __bfloat16_as_ushort(l));
                         split_bf16(im, h, l);
-                        g.out_hi[o + N] = h;
-                        g.out_lo[o + N] = l;
+                        st_shared_u16(a + 1024, __bfloat16_as_ushort(h));
+                        st_shared_u16(a + 3072, __bfloat16_as_ushort(l));
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int row = j * N + v0;
+                        tma_store_2d(&mapOhi, m0, row, stg);
+                        tma_store_2d(&mapOhi, N + m0, row, stg + 1024);
+                        tma_store_2d(&mapOlo, m0, row, stg + 2048);
+                        tma_store_2d(&mapOlo, N + m0, row, stg + 3072);
+                        bulk_commit();
                     }
                 } else if constexpr (EPI == kEpiModulus) {
                     // rows are column frequencies v = m, columns row frequencies
@@ -385,26 +432,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                         split_bf16(pre, hr[ii], lr[ii]);
                         split_bf16(pim, hi_[ii], li[ii]);
                     }
-                    const size_t o = ((size_t)j * N + m) * (2 * N) + v0;
-                    uint4* dh = reinterpret_cast<uint4*>(g.out_hi + o);
-                    uint4* dl = reinterpret_cast<uint4*>(g.out_lo + o);
-                    uint4* dhi = reinterpret_cast<uint4*>(g.out_hi + o + N);
-                    uint4* dli = reinterpret_cast<uint4*>(g.out_lo + o + N);
-                    dh[0] = reinterpret_cast<const uint4*>(hr)[0];
-                    dh[1] = reinterpret_cast<const uint4*>(hr)[1];
-                    dl[0] = reinterpret_cast<const uint4*>(lr)[0];
-                    dl[1] = reinterpret_cast<const uint4*>(lr)[1];
-                    dhi[0] = reinterpret_cast<const uint4*>(hi_)[0];
-                    dhi[1] = reinterpret_cast<const uint4*>(hi_)[1];
-                    dli[0] = reinterpret_cast<const uint4*>(li)[0];
-                    dli[1] = reinterpret_cast<const uint4*>(li)[1];
-                } else {
-                    // y[j][m][v0 + ii]
-                    float4* yo = reinterpret_cast<float4*>(g.y + (size_t)j * NN + (size_t)m * N + v0);
+                    // rows m0 .. m0 + 31, columns v0 .. v0 + 15 (re) and N + v0 .. (im):
+                    // four [32 m][16 v] bf16 arrays (hi re, hi im, lo re, lo im)
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+                    const uint4* q4[4] = {reinterpret_cast<const uint4*>(hr), reinterpret_cast<const uint4*>(hi_),
+                                          reinterpret_cast<const uint4*>(lr), reinterpret_cast<const uint4*>(li)};
 #pragma unroll
-                    for (int ii = 0; ii < 8; ++ii)
-                        yo[ii] = make_float4(__uint_as_float(r[4 * ii]), __uint_as_float(r[4 * ii + 1]),
-                                             __uint_as_float(r[4 * ii + 2]), __uint_as_float(r[4 * ii + 3]));
+                    for (int a = 0; a < 4; ++a) {
+                        const uint32_t d = stg + (uint32_t)(a * 1024 + lane * 32);
+                        st_shared_v4(d, q4[a][0].x, q4[a][0].y, q4[a][0].z, q4[a][0].w);
+                        st_shared_v4(d + 16, q4[a][1].x, q4[a][1].y, q4[a][1].z, q4[a][1].w);
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int row = j * N + m0;
+                        tma_store_2d(&mapOhi, v0, row, stg);
+                        tma_store_2d(&mapOhi, N + v0, row, stg + 1024);
+                        tma_store_2d(&mapOlo, v0, row, stg + 2048);
+                        tma_store_2d(&mapOlo, N + v0, row, stg + 3072);
+                        bulk_commit();
+                    }
+                } else {
+                    // y rows m0 .. m0 + 31 of wave j, floats 2 v0 .. 2 v0 + 31: one
+                    // [32][32] float tile, 128-byte swizzled (conflict-free writes)
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        st_shared_v4(stg + (uint32_t)(lane * 128 + ((q ^ (lane & 7)) << 4)), r[4 * q],
+                                     r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&mapOhi, 2 * v0, j * N + m0, stg);
+                        bulk_commit();
+                    }
                 }
             }
             // hand the accumulator back to the MMA warp
@@ -421,6 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     g.e_part[((size_t)rb * nt_per + nt) * kEpiWarps + 4 * half + qw] = (double)e;
             }
         }
+        // every tile store of this warp has completed before the CTA leaves
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -521,6 +588,22 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t cols, ui
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Store map of an epilogue output: rows x cols elements (bf16 or f32), tile
+// box_cols x box_rows, 128-byte swizzle or none.
+bool make_store_map(CUtensorMap* m, void* base, bool f32, uint64_t rows, uint64_t cols, uint32_t box_cols,
+                    uint32_t box_rows, bool sw128) {
+    PFN_encodeTiled enc = get_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * (f32 ? 4 : 2)};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool bf16x3_supported(int N) { return N == 128 || N == 256; }
@@ -599,6 +682,15 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI,
         if (!make_map(&mA[i], planes[i], rows, cols, kBM)) return cudaErrorInvalidValue;
         if (!make_map(&mB[i], B[i], cols, cols, kBN / 2)) return cudaErrorInvalidValue;
     }
+    // epilogue stores: split-transpose tiles [16 rows][32 cols] into buffer 1,
+    // modulus tiles [32 rows][16 cols] into buffer 0, y tiles [32][32] floats
+    CUtensorMap mS[2], mM[2], mY;
+    for (int i = 0; i < 2; ++i) {
+        if (!make_store_map(&mS[i], planes[2 + i], false, rows, cols, 32, 16, false))
+            return cudaErrorInvalidValue;
+        if (!make_store_map(&mM[i], planes[i], false, rows, cols, 16, 32, false)) return cudaErrorInvalidValue;
+    }
+    if (!make_store_map(&mY, a.y, true, rows, cols, 32, 32, true)) return cudaErrorInvalidValue;
     GemmArgs g{};
     g.N = N;
     g.J = a.J;
@@ -633,20 +725,20 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI,
     // 1: Z = X F -> Z^T into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[0], mB[1], g)) != cudaSuccess)
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[0], mB[1], mS[0], mS[1], g)) != cudaSuccess)
         return e;
     // 2: Psi^T = Z^T F, modulus -> Psi''^T into buffer 0
     g.out_hi = p[0];
     g.out_lo = p[1];
-    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiModulus>, mA[2], mA[3], mB[0], mB[1], g)) != cudaSuccess)
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiModulus>, mA[2], mA[3], mB[0], mB[1], mM[0], mM[1], g)) != cudaSuccess)
         return e;
     // 3: G^T = Psi''^T conj(F) -> G into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
-    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[2], mB[3], g)) != cudaSuccess)
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiSplitT>, mA[0], mA[1], mB[2], mB[3], mS[0], mS[1], g)) != cudaSuccess)
         return e;
     // 4: y = G conj(F)
-    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiOut>, mA[2], mA[3], mB[2], mB[3], g)) != cudaSuccess)
+    if ((e = cudaLaunchKernelEx(&cfg, dft_gemm_kernel<kEpiOut>, mA[2], mA[3], mB[2], mB[3], mY, mY, g)) != cudaSuccess)
         return e;
     return cudaGetLastError();
 }
