@@ -32,7 +32,9 @@
 // accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16) from one
 // thread, warps 2-9 (two per tensor-memory lane quarter, even and odd
 // column chunks) drain one accumulator with tcgen05.ld and run the
-// epilogue while the MMAs of the next tile fill the other.  Every wait
+// epilogue while the MMAs of the next tile fill the other; each epilogue
+// warp stages its 32-row chunk in shared memory in the output's layout and
+// writes it with TMA tile stores.  Every wait
 // on an mbarrier is bounded in time; on expiry the kernel records an error
 // flag, drains and returns (the host reports PTYCHO_ETIMEOUT).
 #include <cuda.h>
