@@ -170,27 +170,69 @@ __global__ void __launch_bounds__(kT) probe_partial_kernel(
     partPd[(size_t)ch * NN + r] = den;
 }
 
+// FP64 totals of the probe partials: a block takes kT / RG probe pixels, its
+// RG thread groups each add a contiguous range of chunks in order, and the
+// group totals are added in group order (a fixed order: deterministic; RG = 1
+// when there are few chunks, 8 when there are many).  The same blocks also
+// add the per-CTA Fourier-error partials of the divide step in fixed slices,
+// one FP64 slice total per block, so the final sum (in the normalise kernel)
+// is over one value per block.
+template <int RG>
 __global__ void __launch_bounds__(kT) probe_reduce_kernel(
     const float2* __restrict__ partP, const float* __restrict__ partPd, int NN, int chunks,
-    double2* __restrict__ numP, double* __restrict__ denP, unsigned long long* __restrict__ maxP) {
-    __shared__ double scratch[kT / 32];
-    const int r = blockIdx.x * kT + threadIdx.x;
-    double mx = 0.0;
+    double2* __restrict__ numP, double* __restrict__ denP, unsigned long long* __restrict__ maxP,
+    const double* __restrict__ e_part, int n_part, double* __restrict__ e_slice) {
+    constexpr int RP = kT / RG;
+    __shared__ double gx[RG][RP], gy[RG][RP], gd[RG][RP];
+    __shared__ double scratch_s[kT / 32], scratch_m[kT / 32];
+    const int px = threadIdx.x % RP, grp = threadIdx.x / RP;
+    const int r = blockIdx.x * RP + px;
+    const int c0 = (grp * chunks) / RG, c1 = ((grp + 1) * chunks) / RG;
+    double nx = 0.0, ny = 0.0, d = 0.0;
     if (r < NN) {
-        double nx = 0.0, ny = 0.0, d = 0.0;
-        for (int ch = 0; ch < chunks; ++ch) {
+        for (int ch = c0; ch < c1; ++ch) {
             const float2 p = partP[(size_t)ch * NN + r];
             nx += (double)p.x;
             ny += (double)p.y;
             d += (double)partPd[(size_t)ch * NN + r];
         }
-        numP[r] = make_double2(nx, ny);
-        denP[r] = d;
-        mx = d;
     }
-    const double bm = block_max_double(mx, scratch);
+    double mx = 0.0;
+    if constexpr (RG == 1) {
+        if (r < NN) {
+            numP[r] = make_double2(nx, ny);
+            denP[r] = d;
+            mx = d;
+        }
+    } else {
+        gx[grp][px] = nx;
+        gy[grp][px] = ny;
+        gd[grp][px] = d;
+        __syncthreads();
+        if (grp == 0 && r < NN) {
+            double tx = 0.0, ty = 0.0, td = 0.0;
+#pragma unroll
+            for (int g = 0; g < RG; ++g) {
+                tx += gx[g][px];
+                ty += gy[g][px];
+                td += gd[g][px];
+            }
+            numP[r] = make_double2(tx, ty);
+            denP[r] = td;
+            mx = td;
+        }
+    }
+    const int per = (n_part + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int e0 = (int)blockIdx.x * per, e1 = min(n_part, e0 + per);
+    double es = 0.0;
+    for (int i = e0 + (int)threadIdx.x; i < e1; i += kT) es += e_part[i];
+    const double slice = block_sum_double<kT>(es, scratch_s);
+    if (threadIdx.x == 0) e_slice[blockIdx.x] = slice;
+    const double bm = block_max_double(mx, scratch_m);
     if (threadIdx.x == 0) atomicMax(maxP, (unsigned long long)__double_as_longlong(bm));
 }
+
+constexpr int kManyChunks = 8;  // above this the chunks are added by 8 thread groups
 
 // Probe update, plus (block 0) the iteration's Fourier error, stored in the
 // ring at the slot of the device-side iteration counter (so a captured graph
@@ -198,7 +240,7 @@ __global__ void __launch_bounds__(kT) probe_reduce_kernel(
 __global__ void __launch_bounds__(kT) probe_normalise_kernel(
     const double2* __restrict__ numP, const double* __restrict__ denP,
     const unsigned long long* __restrict__ maxP, int NN, double alpha, float2* __restrict__ P,
-    const double* __restrict__ e_part, int n_part, double inv_sumI, double* __restrict__ e_ring,
+    const double* __restrict__ e_slice, int n_slice, double inv_sumI, double* __restrict__ e_ring,
     unsigned long long* __restrict__ d_iter, int ring_cap, unsigned* __restrict__ maxO) {
     __shared__ double scratch[kT / 32];
     const int r = blockIdx.x * kT + threadIdx.x;
@@ -210,7 +252,7 @@ __global__ void __launch_bounds__(kT) probe_normalise_kernel(
     }
     if (blockIdx.x == 0) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < n_part; i += kT) s += e_part[i];
+        for (int i = threadIdx.x; i < n_slice; i += kT) s += e_slice[i];
         const double tot = block_sum_double<kT>(s, scratch);
         if (threadIdx.x == 0) {
             const unsigned long long k = *d_iter;
@@ -280,6 +322,11 @@ __global__ void __launch_bounds__(kT) materialise_kernel(float2* __restrict__ x,
 
 }  // namespace
 
+int probe_reduce_blocks(int N, int chunks) {
+    const int rp = chunks > kManyChunks ? kT / 8 : kT;
+    return (N * N + rp - 1) / rp;
+}
+
 int probe_chunks(int J, int N) {
     const int blocks = (N * N + kT - 1) / kT;
     int ch = (2048 + blocks - 1) / blocks;  // about 2048 CTAs in the partial pass
@@ -310,10 +357,15 @@ cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos
                                                                          cb.maxP);
     probe_partial_kernel<<<dim3((NN + kT - 1) / kT, cb.chunks), kT, 0, st>>>(
         y, O, pos, J, N, Mc, cb.chunks, cb.partP, cb.partPd);
-    probe_reduce_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cb.partP, cb.partPd, NN, cb.chunks,
-                                                          cb.numP, cb.denP, cb.maxP);
+    const int n_slice = probe_reduce_blocks(N, cb.chunks);
+    if (cb.chunks > kManyChunks)
+        probe_reduce_kernel<8><<<n_slice, kT, 0, st>>>(cb.partP, cb.partPd, NN, cb.chunks, cb.numP,
+                                                       cb.denP, cb.maxP, e_part, n_part, cb.e_slice);
+    else
+        probe_reduce_kernel<1><<<n_slice, kT, 0, st>>>(cb.partP, cb.partPd, NN, cb.chunks, cb.numP,
+                                                       cb.denP, cb.maxP, e_part, n_part, cb.e_slice);
     probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cb.numP, cb.denP, cb.maxP, NN,
-                                                             (double)alpha, P, e_part, n_part,
+                                                             (double)alpha, P, cb.e_slice, n_slice,
                                                              inv_sumI, e_ring, d_iter, ring_cap,
                                                              cb.maxO);
     return cudaGetLastError();

@@ -59,6 +59,7 @@ struct ConcurBufs {
     double2* numP;         // [N*N]
     double* denP;          // [N*N]
     unsigned long long* maxP;  // bits of max(denP) (double, >= 0)
+    double* e_slice;       // [probe_reduce_blocks(N, chunks)] FP64 slice totals of the Fourier-error partials
     int* tile_ptr;         // [tiles + 1] CSR of positions overlapping each object tile
     int4* tile_win;        // CSR entries (position j, window row, window col, 0)
     int tiles_r, tiles_c, chunks;
@@ -72,6 +73,7 @@ struct ConcurBufs {
 constexpr int kObjTileR = PTYCHO_OBJ_TILE_R;  // object tile rows of the gather
 constexpr int kObjTile = PTYCHO_OBJ_TILE_C;   // object tile columns
 int probe_chunks(int J, int N);
+int probe_reduce_blocks(int N, int chunks);  // blocks of the probe reduction (one error slice each)
 cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
                           const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
                           const double* e_part, int n_part, double inv_sumI, double* e_ring,

@@ -267,6 +267,7 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
     b += M * (sizeof(float2) + sizeof(float)) + 16;
     b += chunks * NN * (sizeof(float2) + sizeof(float));
     b += NN * (sizeof(double2) + sizeof(double));
+    b += (size_t)probe_reduce_blocks(N, (int)chunks) * sizeof(double);  // error slice totals
     b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * (N / kObjTile + 1) * sizeof(int4);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
     b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
@@ -373,6 +374,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.partP, (size_t)chunks * NN);
     PT_ALLOC(ctx->cb.partPd, (size_t)chunks * NN);
     PT_ALLOC(ctx->cb.numP, NN);
+    PT_ALLOC(ctx->cb.e_slice, (size_t)probe_reduce_blocks(N, chunks));
     PT_ALLOC(ctx->cb.denP, NN);
     PT_ALLOC(ctx->cb.maxP, (size_t)1);
     PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
