@@ -1,10 +1,11 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (one context, FP32, 1024 exit waves of 256 x 256 on a 1300 x 1300
-object; and the 4096-wave precision workload on the tensor-core path).
+object; the 4096-wave precision workload on the tensor-core path; and the
+4096-wave 128 x 128 workload on the FP32 path).
 
 The FP64 oracle runs one whole RAAR iteration of the 1024-wave scan (about
 half a minute on the host), so exit waves, object and probe are compared in
-full; on the 4096-wave scan the oracle computes the divided exit waves of a
+full; on the 4096-wave scans the oracle computes the divided exit waves of a
 sample of positions one by one.  Tolerances as in the small-size parity
 tests: relative L2 <= 1e-5 (FP32) and <= 5e-3 (BF16 x 3).
 """
@@ -62,3 +63,21 @@ def test_precision_workload_sampled_divide():
         yj = oabc.relax(lambda v: optycho.project_D(v, sq)[0], 2.0)(xj)
         assert rel_l2(y[j], yj[0]) <= 5e-3
         assert rel_l2(y[j], yj[0]) <= 1e-4
+
+
+def test_large128_sampled_divide():
+    """4096 exit waves of 128 x 128 (the 128^2 bench workload, clusters of 8
+    CTAs): the divided exit waves of sampled positions against the oracle,
+    FP32 tolerance."""
+    scan = synth.make_scan(synth.named_spec("large128"))
+    sample = [0, 1, 7, 8, 63, 64, 2047, 2048, 4031, 4095]
+    with gpu_recon(scan) as r:
+        r.iterate(1.0, 0.0, 2.0, 1)   # x_1 = y_0 = P^2_D x_0
+        y = r.exit_waves()
+    P0 = scan.probe0.astype(np.complex128)
+    O0 = scan.obj0.astype(np.complex128)
+    for j in sample:
+        xj = optycho.exit_waves(P0, O0, scan.pos[j:j + 1])
+        sq = np.sqrt(scan.intensity[j:j + 1].astype(np.float64))
+        yj = oabc.relax(lambda v: optycho.project_D(v, sq)[0], 2.0)(xj)
+        assert rel_l2(y[j], yj[0]) <= 1e-5
