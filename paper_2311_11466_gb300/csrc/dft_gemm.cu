@@ -535,28 +535,15 @@ __global__ void __launch_bounds__(256) bf16_prologue_kernel(
     alo[o + N] = l;
 }
 
-// sqrt(I) in the patterns' own layout; flags bad values and writes FP64
-// partial sums of I per (pattern, 32 x 32 tile).
+// sqrt(I) in the patterns' own layout (the intensities were already checked
+// for negative and non-finite values by the permuting kernel of the FP32
+// path, which reads the same array).
 __global__ void __launch_bounds__(256) sqrt_intensity_kernel(const float* __restrict__ I,
-                                                             float* __restrict__ out, int N,
-                                                             double* __restrict__ psum,
-                                                             int* __restrict__ bad) {
-    __shared__ double red[8];
-    const int j = blockIdx.z;
-    const int u0 = blockIdx.y * 32, v0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const size_t base = (size_t)j * N * N;
-    double s = 0.0;
-    for (int k = ty; k < 32; k += 8) {
-        const size_t o = base + (size_t)(u0 + k) * N + v0 + tx;
-        const float val = I[o];
-        if (!(val >= 0.0f) || !isfinite(val)) atomicOr(bad, 1);
-        s += (double)val;
-        out[o] = sqrtf(fmaxf(val, 0.0f));
-    }
-    const double tot = block_sum_double<256>(s, red);
-    if (threadIdx.x == 0)
-        psum[((size_t)j * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+                                                             float* __restrict__ out, size_t n) {
+    // scalar accesses: a caller's device pointer to the intensities need not
+    // be 16-byte aligned
+    for (size_t i = blockIdx.x * (size_t)256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
+        out[i] = sqrtf(fmaxf(I[i], 0.0f));
 }
 
 using PFN_encodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -661,10 +648,11 @@ cudaError_t bf16x3_prepare() {
                                 (int)kSmem);
 }
 
-cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, double* psum, int* bad, int J,
-                                  cudaStream_t st) {
-    dim3 grid(N / 32, N / 32, J);
-    sqrt_intensity_kernel<<<grid, 256, 0, st>>>(I, out, N, psum, bad);
+cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, int J, cudaStream_t st) {
+    const size_t n = (size_t)J * N * N;
+    const size_t want = (n + 255) / 256;
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    sqrt_intensity_kernel<<<grid, 256, 0, st>>>(I, out, n);
     return cudaGetLastError();
 }
 

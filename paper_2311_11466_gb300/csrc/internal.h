@@ -97,8 +97,7 @@ int bf16x3_error_parts(int N, int J);
 void bf16x3_constants(int N, std::vector<uint16_t>& fwd_hi, std::vector<uint16_t>& fwd_lo,
                       std::vector<uint16_t>& inv_hi, std::vector<uint16_t>& inv_lo);
 cudaError_t bf16x3_prepare();
-cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, double* psum, int* bad, int J,
-                                  cudaStream_t st);
+cudaError_t launch_sqrt_intensity(int N, const float* I, float* out, int J, cudaStream_t st);
 cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI,
                                  uint16_t* const planes[4], const uint16_t* const B[4],
                                  int* err_flag, cudaStream_t st);

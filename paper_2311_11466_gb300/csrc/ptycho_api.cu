@@ -275,7 +275,6 @@ size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, i
         b += (size_t)J * NN * sizeof(float);           // sqrt(I), patterns' layout
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
         b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
-        b += (size_t)J * (NN / 1024 + 1) * sizeof(double);
         const size_t parts = (size_t)bf16x3_error_parts(N, J);  // a second, larger error buffer
         if (parts > (size_t)J * C) b += parts * sizeof(double);
     }
@@ -380,12 +379,10 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
     PT_ALLOC(ctx->cb.tile_win, tile_list.size() > 0 ? tile_list.size() : 1);
     PT_ALLOC(psum, (size_t)J * sq_blocks);
-    double* psum_t = nullptr;
     if (tc) {
         PT_ALLOC(ctx->sqrtI, (size_t)J * NN);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->Bc[i], 4 * NN);
-        PT_ALLOC(psum_t, (size_t)J * (NN / 1024));
         const int tiles = bf16x3_error_parts(N, J);
         if (tiles > J * C) {
             double* more = nullptr;
@@ -443,7 +440,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_STEP(launch_sqrt_permute(N, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
     if (tc) {
         PT_STEP(bf16x3_prepare());
-        PT_STEP(launch_sqrt_intensity(N, Idev, ctx->sqrtI, psum_t, ctx->dflag, J, st));
+        PT_STEP(launch_sqrt_intensity(N, Idev, ctx->sqrtI, J, st));
         std::vector<uint16_t> Bh[4];
         bf16x3_constants(N, Bh[0], Bh[1], Bh[2], Bh[3]);
         for (int i = 0; i < 4; ++i)
