@@ -27,8 +27,12 @@ PTYCHO_LOAD_INTENSITY_DEVICE = 1
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE"}
 
 # (a, b, c) of the named algorithms; DC is the paper's own definition
-# (Introduction), the others are readings of the general update (see
-# the design doc).  Data, not code: every setting runs the same kernels.
+# (Introduction), the others are readings of the general update: expanding
+# a P^b_C P^c_D x + (1 - a) x gives DR = (R_C R_D + I) / 2 for (1/2, 2, 2),
+# RAAR(beta) = (beta/2)(R_C R_D + I) + (1 - beta) P_D for (1/2, 2 beta, 2),
+# RRR(beta) = x + beta (P_C R_D x - P_D x) for (beta/2, 2, 2), SF = R_C P_D for
+# (1, 2, 1) and AR = R_C R_D for (1, 2, 2).  Data, not code: every setting
+# runs the same kernels.
 PRESETS = {
     "DC": (1.0, 1.0, 1.0),
     "AR": (1.0, 2.0, 2.0),
