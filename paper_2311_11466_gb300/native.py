@@ -161,7 +161,10 @@ def ptycho_load_scan(h, pos, intensity, obj0, probe0) -> None:
     if isinstance(intensity, np.ndarray):
         inten = np.ascontiguousarray(intensity, dtype=np.float32)
         N = inten.shape[-1]
-    else:  # a CUDA tensor: pass its device pointer
+    else:  # a CUDA tensor: pass its device pointer (dense float32 only)
+        if (str(getattr(intensity, "dtype", "")) != "torch.float32" or not intensity.is_contiguous()
+                or not getattr(intensity, "is_cuda", False)):
+            raise ValueError("a device intensity must be a contiguous float32 CUDA tensor")
         inten = intensity
         N = int(intensity.shape[-1])
         flags |= PTYCHO_LOAD_INTENSITY_DEVICE

@@ -209,6 +209,30 @@ def test_zero_exit_waves_take_sqrt_I(tiny):
     assert abs(e[0] - 1.0) <= TOL
 
 
+def test_device_intensity_equals_host_intensity(tiny):
+    """Intensities given as a device buffer (PTYCHO_LOAD_INTENSITY_DEVICE)
+    give bitwise the same run as the host copy; a non-contiguous or
+    non-float32 device tensor is refused before the call."""
+    torch = pytest.importorskip("torch")
+    abc = native.PRESETS["RAAR"]
+    with gpu_recon(tiny) as r:
+        r.iterate(*abc, 3)
+        O_h, P_h = r.object_probe()
+        e_h = r.errors()
+    dev = torch.from_numpy(tiny.intensity).cuda()
+    with native.Reconstruction() as r:
+        r.load_scan(tiny.pos, dev, tiny.obj0, tiny.probe0)
+        r.iterate(*abc, 3)
+        O_d, P_d = r.object_probe()
+        e_d = r.errors()
+    assert np.array_equal(O_h, O_d) and np.array_equal(P_h, P_d) and np.array_equal(e_h, e_d)
+    with native.Reconstruction() as r:
+        with pytest.raises(ValueError):
+            r.load_scan(tiny.pos, dev.transpose(1, 2), tiny.obj0, tiny.probe0)
+        with pytest.raises(ValueError):
+            r.load_scan(tiny.pos, dev.double(), tiny.obj0, tiny.probe0)
+
+
 def test_empty_scan_rejected(tiny):
     N = tiny.N
     with native.Reconstruction() as r:
