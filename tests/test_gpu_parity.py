@@ -233,6 +233,31 @@ def test_device_intensity_equals_host_intensity(tiny):
             r.load_scan(tiny.pos, dev.double(), tiny.obj0, tiny.probe0)
 
 
+def test_external_stream_profile_and_device_bytes(tiny):
+    """A caller-provided stream gives bitwise the same run as the private one;
+    the event hook records one divide and one concur duration per iteration;
+    the device bytes of a loaded scan stay within the admission estimate
+    (ptycho_scan_bytes, an upper bound) and within 5 % of it."""
+    torch = pytest.importorskip("torch")
+    abc = native.PRESETS["DR"]
+    with gpu_recon(tiny) as r:
+        r.iterate(*abc, 4)
+        O_a, P_a = r.object_probe()
+    st = torch.cuda.Stream()
+    with native.Reconstruction(stream=st.cuda_stream) as r:
+        r.load_scan(tiny.pos, tiny.intensity, tiny.obj0, tiny.probe0)
+        native.ptycho_profile_enable(r.h, True)
+        r.iterate(*abc, 4)
+        div_ms, con_ms, n = native.ptycho_profile_read(r.h)
+        native.ptycho_profile_enable(r.h, False)
+        O_b, P_b = r.object_probe()
+        used = native.ptycho_device_bytes(r.h)
+    assert np.array_equal(O_a, O_b) and np.array_equal(P_a, P_b)
+    assert n == 4 and div_ms > 0.0 and con_ms > 0.0
+    est = native.ptycho_scan_bytes(tiny.J, tiny.N, *tiny.M_shape)
+    assert 0.95 * est <= used <= est
+
+
 def test_empty_scan_rejected(tiny):
     N = tiny.N
     with native.Reconstruction() as r:
