@@ -56,6 +56,30 @@ def test_batch_graph_equals_alone(scans):
         r.close()
 
 
+def test_batch_with_tensor_core_context(scans):
+    """A batch mixing an FP32 context and a tensor-core (BF16 x 3) context:
+    the captured graph replays both, each bitwise equal to its run alone."""
+    n = 4
+    sc32, sc16 = scans[0], scans[1]
+    r32 = native.Reconstruction()
+    r32.load_scan(sc32.pos, sc32.intensity, sc32.obj0, sc32.probe0)
+    r16 = native.Reconstruction(precision="bf16x3")
+    r16.load_scan(sc16.pos, sc16.intensity, sc16.obj0, sc16.probe0)
+    abc = native.PRESETS["RAAR"]
+    serve.run_batch([r32, r16], [abc, abc], n)
+    for r, sc, prec in ((r32, sc32, "fp32"), (r16, sc16, "bf16x3")):
+        with native.Reconstruction(precision=prec) as ra:
+            ra.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+            ra.iterate(*abc, n)
+            O, P = ra.object_probe()
+            e = ra.errors()
+        Ob, Pb = r.object_probe()
+        np.testing.assert_array_equal(Ob, O)
+        np.testing.assert_array_equal(Pb, P)
+        np.testing.assert_array_equal(r.errors(), e)
+        r.close()
+
+
 def test_server_results_equal_alone(scans):
     n = 7
     arrivals = [0.0, 0.0, 0.02, 0.05]
@@ -76,5 +100,37 @@ def test_server_rejects_scan_beyond_budget(scans):
         sc = scans[1]
         with pytest.raises(native.PtychoError):
             serve.ptycho_server_submit(s, sc.pos, sc.intensity, sc.obj0, sc.probe0, 1, 1, 1, 5)
+    finally:
+        serve.ptycho_server_destroy(s)
+
+
+def test_server_tensor_core_requests(scans):
+    """A server whose contexts use the tensor-core path (server options carry
+    the precision): two requests (128^2 and 256^2) served in interleaved
+    rounds, each bitwise equal to the same reconstruction run alone."""
+    n = 5
+    abc = native.PRESETS["DR"]
+    o = native.ptycho_default_opts()
+    o.precision = native.PTYCHO_PREC_BF16X3
+    s = serve.ptycho_server_create(8 << 30, 2, o)
+    try:
+        picks = [scans[1], scans[3]]
+        ids = [serve.ptycho_server_submit(s, sc.pos, sc.intensity, sc.obj0, sc.probe0, *abc, n)
+               for sc in picks]
+        for _ in range(100):
+            na, nq = serve.ptycho_server_step(s, 2)
+            if na == 0 and nq == 0:
+                break
+        for rid, sc in zip(ids, picks):
+            O = np.empty(sc.M_shape, dtype=np.complex64)
+            P = np.empty((sc.N, sc.N), dtype=np.complex64)
+            st, _ = serve.ptycho_server_poll(s, rid, O, P)
+            assert st == serve.PTYCHO_REQ_DONE
+            with native.Reconstruction(precision="bf16x3") as r:
+                r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+                r.iterate(*abc, n)
+                Oa, Pa = r.object_probe()
+            np.testing.assert_array_equal(O, Oa)
+            np.testing.assert_array_equal(P, Pa)
     finally:
         serve.ptycho_server_destroy(s)
