@@ -87,6 +87,22 @@ def test_odd_row_block_count():
     assert abs(e[0] - prob.last_error) <= TOL * prob.last_error
 
 
+def test_sp_and_model_error_on_tensor_core_context(scan):
+    """Sequential projections and the model error run the FP32 kernels in
+    either kind of context: from the same start a tensor-core context gives
+    bitwise the FP32 context's object, probe and model error."""
+    out = []
+    for prec in ("fp32", "bf16x3"):
+        with gpu_recon(scan, precision=prec) as r:
+            r.sp_iterate(0.8, 1)
+            O, P = r.object_probe()
+            out.append((O, P, r.model_error()))
+    (O32, P32, m32), (O16, P16, m16) = out
+    np.testing.assert_array_equal(O16, O32)
+    np.testing.assert_array_equal(P16, P32)
+    assert m16 == m32
+
+
 def test_bf16x3_rejects_other_sizes():
     sc = synth.make_scan(small_spec(64, 2, 2, seed=3))
     with native.Reconstruction(precision="bf16x3") as r:
