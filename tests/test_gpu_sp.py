@@ -71,8 +71,9 @@ def test_sp_three_passes_within_oracle_sensitivity(tiny):
     np.testing.assert_allclose(e[0], errs[0], rtol=1e-4)
 
 
-def test_sp_then_abc_and_other_sizes():
-    sc = synth.make_scan(small_spec(256, 2, 3, seed=31, photons=1e6))
+@pytest.mark.parametrize("N", [128, 256])
+def test_sp_then_abc_and_other_sizes(N):
+    sc = synth.make_scan(small_spec(N, 2, 3, seed=31, photons=1e6))
     O = sc.obj0.astype(np.complex128)
     P = sc.probe0.astype(np.complex128)
     osp.sp_iterate(O, P, sc.pos, sc.intensity.astype(np.float64), 1.0)
@@ -83,7 +84,7 @@ def test_sp_then_abc_and_other_sizes():
         r.iterate(*native.PRESETS["DC"], 1)
     assert rel_l2(Og, O) <= 1e-4
     assert rel_l2(Pg, P) <= 1e-4
-    ref = np.stack([P * O[a:a + 256, b:b + 256] for a, b in sc.pos])
+    ref = np.stack([P * O[a:a + N, b:b + N] for a, b in sc.pos])
     assert rel_l2(x, ref) <= 1e-5
 
 
