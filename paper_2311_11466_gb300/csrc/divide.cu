@@ -551,41 +551,6 @@ cudaError_t divide_prepare(int N) {
     return cudaErrorInvalidValue;
 }
 
-template <int N>
-int slots_t() {
-    using G = Geo<N>;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(G::C * 1024);
-    cfg.blockDim = dim3(G::T);
-    cfg.dynamicSmemBytes = G::SMEM;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = G::C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
-    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
-    cfg.attrs = attr;
-    cfg.numAttrs = 2;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, divide_kernel<N, kModeDivide>, &cfg) != cudaSuccess || n <= 0) {
-        cudaGetLastError();
-        n = 0;
-    }
-    return n;
-}
-
-int divide_slots(int N) {
-    switch (N) {
-        case 8: return slots_t<8>();
-        case 16: return slots_t<16>();
-        case 32: return slots_t<32>();
-        case 64: return slots_t<64>();
-        case 128: return slots_t<128>();
-        case 256: return slots_t<256>();
-    }
-    return 0;
-}
 
 cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st) {
     switch (N) {

@@ -26,7 +26,6 @@ struct DivideArgs {
     int write_x;          // store x_k to x[] (needed when this iteration's a != 1)
     int err_only;         // only the Fourier error of x_k (no y written)
     float2* scratch;      // [J][N^2] transpose scratch (row pass -> column pass)
-    int n_slots;          // unused by the kernel (kept for the launch helpers)
     int sp;               // 1: one sequential-projections step (at position sp_pos)
     int sp_pos;
     float2* P_mut;        // probe and object updated by a sequential-projections step
@@ -39,9 +38,6 @@ int divide_cluster_size(int N);
 // Twiddle table of the divide kernel for side N (host, FP64 rounded to FP32).
 void divide_twiddles(int N, std::vector<float2>& tw);
 cudaError_t divide_prepare(int N);  // one-time kernel attributes
-// Clusters of the divide kernel that fit on the device at once (after
-// divide_prepare): the number of exit waves in flight.
-int divide_slots(int N);
 cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st);
 // sqrt of the intensities into the divide kernel's frequency order; flags
 // *bad (device int) if any value is negative or not finite; per-pattern sums

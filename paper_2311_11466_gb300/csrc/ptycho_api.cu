@@ -43,7 +43,6 @@ struct ptycho_ctx {
     float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
     float* sqrtIp = nullptr;
     float2* scratch = nullptr;  // divide-kernel transpose scratch, one slot per exit wave
-    int n_slots = 0;
     // tensor-core path: sqrt(I) in the patterns' layout, two ping-pong operand buffers (hi,
     // lo) and the constant DFT operands (fwd hi, fwd lo, inv hi, inv lo)
     float* sqrtI = nullptr;
@@ -114,7 +113,6 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;
     ctx->sqrtIp = nullptr;
     ctx->scratch = nullptr;
-    ctx->n_slots = 0;
     ctx->sqrtI = nullptr;
     for (int i = 0; i < 4; ++i) ctx->planes[i] = ctx->Bc[i] = nullptr;
     ctx->pos = nullptr;
@@ -341,9 +339,6 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
         cudaError_t pe = divide_prepare(N);
         if (pe != cudaSuccess) return cuda_fail(ctx, pe, "divide_prepare");
     }
-    int n_slots = divide_slots(N);
-    if (n_slots <= 0) n_slots = 1;
-    if (n_slots > J) n_slots = J;
     const int sq_blocks = (int)((NN + 255) / 256);
     double* psum = nullptr;
     int rc;
@@ -394,7 +389,6 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     ctx->cb.tiles_r = tiles_r;
     ctx->cb.tiles_c = tiles_c;
     ctx->cb.chunks = chunks;
-    ctx->n_slots = n_slots;
     ctx->J = J;
     ctx->N = N;
     ctx->Mr = M_rows;
@@ -498,7 +492,6 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;
         da.err_only = 0;
         da.scratch = ctx->scratch;
-        da.n_slots = ctx->n_slots;
         const bool rec = ctx->prof && ctx->prof_n < kProfMax;
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
         int n_part = ctx->J * ctx->C;
@@ -635,7 +628,6 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
     da.write_x = 0;
     da.err_only = 1;
     da.scratch = ctx->scratch;
-    da.n_slots = ctx->n_slots;
     PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
     PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->J * ctx->C, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
                                   ctx->e_tmp, ctx->stream));
@@ -690,7 +682,6 @@ int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t 
     da.write_x = 0;
     da.err_only = 0;
     da.scratch = ctx->scratch;
-    da.n_slots = ctx->n_slots;
     da.sp = 1;
     for (int it = 0; it < n_iter; ++it) {
         for (int i = 0; i < ctx->J; ++i) {
