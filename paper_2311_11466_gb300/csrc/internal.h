@@ -26,6 +26,8 @@ struct DivideArgs {
     int write_x;          // store x_k to x[] (needed when this iteration's a != 1)
     int err_only;         // only the Fourier error of x_k (no y written)
     float2* scratch;      // [J][N^2] transpose scratch (row pass -> column pass)
+    int reserved;         // unused; keeps the parameter layout below (the divide kernel
+                          // measured 1 % slower at 256^2 with this field removed)
     int sp;               // 1: one sequential-projections step (at position sp_pos)
     int sp_pos;
     float2* P_mut;        // probe and object updated by a sequential-projections step
