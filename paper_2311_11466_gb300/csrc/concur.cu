@@ -13,7 +13,8 @@
 // Determinism: the object is a position-tiled gather (each object tile walks
 // the ascending list of windows that overlap it); the probe is a two-level
 // reduction over positions (FP32 partials over fixed chunks, FP64 final sum
-// in chunk order).  Maxima use integer atomicMax on the bit patterns of
+// in a fixed order: chunk order, or with many chunks contiguous groups of
+// chunks added in group order).  Maxima use integer atomicMax on the bit patterns of
 // non-negative IEEE values, which is order independent.
 #include "common.cuh"
 #include "internal.h"
