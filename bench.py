@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -39,6 +40,7 @@ UNIT = "position-updates/s"
 RAAR = (0.5, 1.8, 2.0)
 FALLBACK_HBM_GBS = 6800.0
 KERNELS_PER_ITER = 6   # divide + object gather + object normalise + probe partial/reduce/normalise
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def _dist():
@@ -598,6 +600,13 @@ def main():
                        "l2": "working set 1.3 GB > L2 (no flush needed)"},
             "roofline": roof,
             "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
+            # the survey's FFT rate: 10 N^2 log2(N^2) flops per position-update (a
+            # forward and an inverse 2-D FFT at 5 N^2 log2(N^2) each), against the
+            # nominal FP32 CUDA-core peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)
+            "fft_rate": {"tflops": value * 10.0 * NN * math.log2(NN) / 1e12,
+                         "flops_per_update": 10.0 * NN * math.log2(NN),
+                         "of_fp32_nominal_peak": value * 10.0 * NN * math.log2(NN) / 1e12 / FP32_NOMINAL_TFLOPS,
+                         "peak_source": "nominal (not measured)"},
             "per_step_bytes": (div_px + 16.0) * J * NN,
             "step_hbm_gbs": (div_px + 16.0) * J * NN / (ms / args.steps / 1e3) / 1e9,
             "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)) * args.steps,
