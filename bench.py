@@ -275,8 +275,9 @@ def run_reference(args, spec):
     scan = synth.make_scan(spec)
     side = 4
     # warm-up steps, then K timed steps, each one oracle iteration of the sample
-    oracle_rate(scan, side, 0.0, max(args.warmup, 0)) if args.warmup > 0 else None
-    rate, n, npos = oracle_rate(scan, side, 0.0, args.steps)
+    # exactly W untimed and K timed iterations (no time bound)
+    oracle_rate(scan, side, float("inf"), max(args.warmup, 0)) if args.warmup > 0 else None
+    rate, n, npos = oracle_rate(scan, side, float("inf"), max(args.steps, 1))
     sample = (f"{npos} positions ({side}x{side} block of the 32x32 raster, 256^2 patterns, "
               f"full 1300^2 object), {n} RAAR iterations of the FP64 oracle")
     line = {
