@@ -22,12 +22,11 @@
 // re-split of the previous iteration, exactly as the FP32 kernel does) and
 // writes its hi/lo planes.
 //
-// GEMM kernel: persistent, one CTA per SM, in clusters of two; each pair
-// works on two 128 x 256 output tiles (128 rows x 128 complex columns) that
-// share the same B tile: each CTA loads its own A tile and one half of the B
-// tile, multicast into both CTAs' shared memory (the MMA commits are
-// multicast too, so a stage is refilled only when both CTAs are done with
-// it).  Warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring that
+// GEMM kernel: persistent, one CTA per SM; CTAs 2p and 2p + 1 take the two
+// 128 x 256 output tiles (128 rows x 128 complex columns) of one work item,
+// which share the same B tile: each CTA loads its own A tile and the whole B
+// tile with plain TMA loads into its own shared memory (the second read of a
+// B tile comes from L2).  Warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring that
 // runs on across tiles, warp 1 allocates all 512 tensor-memory columns (two
 // accumulators) and issues tcgen05.mma (M = 128, N = 256, K = 16) from one
 // thread, warps 2-9 (two per tensor-memory lane quarter, even and odd
@@ -130,26 +129,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
-// The same load into this CTA and its cluster partner (same shared-memory
-// offset and mbarrier offset in both), for operand halves shared by a pair.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                               uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar), "h"(mask)
-        : "memory");
-}
-// Arrive on the mbarrier at this offset in every CTA of the mask once the
-// issued MMAs complete.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), descriptor version 1.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
@@ -236,12 +215,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
 
-    // CTA pairs (clusters of 2) take the two row blocks 2 p and 2 p + 1 of one
-    // output column block: each loads its A tile and one half of the shared B
-    // tile, multicast to both.
-    unsigned int rank;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-    const uint16_t pair_mask = 0x3;
+    // CTAs 2 p and 2 p + 1 take the two row blocks 2 q and 2 q + 1 of one
+    // output column block (the same B tile, read twice, the second time from L2).
+    const unsigned int rank = blockIdx.x & 1u;
 
     const int N = g.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -257,12 +233,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 2);   // the MMAs of both CTAs of the pair
+            mbar_init(empty0 + 8 * s, 1);   // one tcgen05.commit of this CTA's MMAs
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(afull0 + 8 * b, 1);   // one tcgen05.commit
             mbar_init(aempty0 + 8 * b, kEpiWarps);  // one arrival per epilogue warp
         }
+        // make the initialised barriers visible to the async (TMA, tensor-core) proxy
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -273,8 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    // both CTAs' barriers are initialised before any multicast can reach them
-    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    __syncthreads();  // barriers initialised and the tensor-memory address written
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
@@ -294,8 +270,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(full0 + 8 * s, kABytes + kBBytes);
                 const int pair = kb / KBP, kin = (kb % KBP) * kBK;
                 tma_load_2d(sA + s * kABytes, pair == 2 ? &mapAlo : &mapAhi, kin, row0, full0 + 8 * s);
-                tma_load_2d_mc(sB + s * kBBytes + rank * (kBBytes / 2), pair == 1 ? &mapBlo : &mapBhi,
-                               kin, nt * kBN + (int)rank * (kBN / 2), full0 + 8 * s, pair_mask);
+                // the B tile in two boxes of 128 rows
+                const CUtensorMap* mb = pair == 1 ? &mapBlo : &mapBhi;
+                tma_load_2d(sB + s * kBBytes, mb, kin, nt * kBN, full0 + 8 * s);
+                tma_load_2d(sB + s * kBBytes + kBBytes / 2, mb, kin, nt * kBN + kBN / 2, full0 + 8 * s);
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -321,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bd = desc_sw128(sB + s * kBBytes + kk * 32);
                     mma_bf16(acc, ad, bd, (kb | kk) != 0 ? 1u : 0u);
                 }
-                // the stage is free in both CTAs once these MMAs complete
-                mma_commit_mc(empty0 + 8 * s, pair_mask);
+                // the stage is free once these MMAs complete
+                mma_commit(empty0 + 8 * s);
             }
             mma_commit(afull0 + 8 * ab);     // the accumulator is complete
         }
@@ -499,8 +477,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(2 * kTmemCols)
                      : "memory");
     }
-    // neither CTA leaves while its partner may still signal its barriers
-    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // x_k (load or re-split, the same expression as the FP32 divide kernel) and
@@ -698,20 +674,16 @@ cudaError_t launch_divide_bf16x3(const DivideArgs& a, int N, const float* sqrtI,
         if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
             n_sm = 148;
     }
-    // persistent: one CTA per SM, in pairs
+    // persistent: one CTA per SM, an even number of them (the two row blocks
+    // of a work item go to CTAs 2 p and 2 p + 1)
     const int grid = 2 * (pairs < n_sm / 2 ? pairs : n_sm / 2);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = kSmem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
     // 1: Z = X F -> Z^T into buffer 1
     g.out_hi = p[2];
     g.out_lo = p[3];
