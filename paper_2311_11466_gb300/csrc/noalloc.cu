@@ -25,11 +25,15 @@
 
 namespace {
 
-// Capacity: probe side N <= 256; partial sums for chunks * N^2 <= 8 * 256^2
-// (the chunk count of the context path never exceeds this).
+// Capacity: probe side N <= 256.  The partial sums hold chunks * N^2 values,
+// where probe_chunks gives chunks <= ceil(2048 / blocks) with blocks =
+// ceil(N^2 / 256); so chunks * N^2 <= chunks * blocks * 256 <= (2048 + blocks - 1)
+// * 256 <= (2048 + 255) * 256 for every N <= 256 (N = 256 itself needs 8 * 256^2).
 constexpr int kMaxN = 256;
 constexpr size_t kMaxPix = (size_t)kMaxN * kMaxN;
-constexpr size_t kMaxPartial = 8 * kMaxPix;
+constexpr size_t kMaxBlocks = (kMaxPix + 255) / 256;
+constexpr size_t kMaxPartial = (2048 + kMaxBlocks - 1) * 256;
+static_assert(kMaxPartial >= 8 * kMaxPix, "N = 256 with 8 chunks fits");
 
 // Byte layout of the scratch array.
 constexpr size_t kOffPart = 0;                                   // float2 [kMaxPartial]
@@ -38,7 +42,8 @@ constexpr size_t kOffNum = kOffPartD + kMaxPartial * 4;          // double2 [kMa
 constexpr size_t kOffDen = kOffNum + kMaxPix * 16;               // double [kMaxPix]
 constexpr size_t kOffMax = kOffDen + kMaxPix * 8;                // u64 max bits
 constexpr size_t kOffStatus = kOffMax + 8;                       // int status
-constexpr size_t kScratchBytes = kOffStatus + 248;               // 7.5 MiB + 256 B
+constexpr size_t kScratchBytes = kOffStatus + 248;               // 8.25 MiB + 256 B
+static_assert(kOffNum % 16 == 0 && kOffDen % 8 == 0 && kOffMax % 8 == 0, "scratch alignment");
 
 // The scratch itself: one copy on every device that loads the library, held
 // until the process exits.  Host code may not use this name as an address
@@ -166,13 +171,24 @@ extern "C" int ptycho_probe_update_noalloc(const float* y, const float* obj, con
     // the array keeps the previous call's contents: zero the maximum and the status
     if (cudaMemsetAsync(scratch + kOffMax, 0, 16, st) != cudaSuccess) return PTYCHO_ECUDA;
     const unsigned blocks = (unsigned)((NN + kT - 1) / kT);
-    na_partial_kernel<<<dim3(blocks, chunks), kT, 0, st>>>(
-        reinterpret_cast<const float2*>(y), reinterpret_cast<const float2*>(obj),
-        reinterpret_cast<const int2*>(pos_rc), J, N, M_rows, M_cols, chunks, scratch);
-    na_reduce_kernel<<<blocks, kT, 0, st>>>((int)NN, chunks, scratch);
-    na_normalise_kernel<<<blocks, kT, 0, st>>>((int)NN, (double)alpha, scratch,
-                                               reinterpret_cast<float2*>(probe_out));
-    if (cudaGetLastError() != cudaSuccess) return PTYCHO_ECUDA;
+    // each launch reports its own status (an error left on this thread by
+    // earlier, unrelated work is neither returned nor cleared here)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, (unsigned)chunks);
+    cfg.blockDim = dim3(kT);
+    cfg.stream = st;
+    if (cudaLaunchKernelEx(&cfg, na_partial_kernel, reinterpret_cast<const float2*>(y),
+                           reinterpret_cast<const float2*>(obj),
+                           reinterpret_cast<const int2*>(pos_rc), (int)J, (int)N, (int)M_rows,
+                           (int)M_cols, chunks, scratch) != cudaSuccess)
+        return PTYCHO_ECUDA;
+    cfg.gridDim = dim3(blocks);
+    if (cudaLaunchKernelEx(&cfg, na_reduce_kernel, (int)NN, chunks, scratch) != cudaSuccess)
+        return PTYCHO_ECUDA;
+    if (cudaLaunchKernelEx(&cfg, na_normalise_kernel, (int)NN, (double)alpha,
+                           (const unsigned char*)scratch,
+                           reinterpret_cast<float2*>(probe_out)) != cudaSuccess)
+        return PTYCHO_ECUDA;
     int status = 0;
     if (cudaMemcpyAsync(&status, scratch + kOffStatus, sizeof(int), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||

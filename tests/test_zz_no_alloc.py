@@ -6,10 +6,14 @@ must not allocate once it is running.  For them the library offers one entry
 point that takes device buffers for every input and output and keeps its
 scratch in a static device array.  This file checks it through the C ABI,
 with device buffers the test provides, on two calls in a row (two different
-scans, so the second call runs on the scratch the first one left behind),
+scans, so the second call runs on the scratch the first one left behind):
 against the probe that the context-based entry points (ptycho_iterate, then
 ptycho_get_object_probe) compute from the same divided exit waves and object,
-within the parity tolerance of the other GPU tests (relative L2 <= 1e-5).
+and against the FP64 oracle's probe update (oracle.ptycho.concur_probe) on
+seeded synthetic exit waves and objects, including probe sides that the
+context path does not take (N = 48 with J = 300, N = 255 with J = 16: the
+sizes where the partial sums fill the most of the scratch), all within the
+parity tolerance of the other GPU tests (relative L2 <= 1e-5).
 
 The file name makes pytest collect it last.
 """
@@ -75,6 +79,28 @@ def test_matches_context_path_on_two_calls_in_a_row():
         rc, P = _no_alloc(y, O, scan.pos, alpha)
         assert rc == native.PTYCHO_OK
         assert _rel(P, P_ref) <= TOL, (scan.N, _rel(P, P_ref))
+
+
+def _synthetic(N, J, M, seed):
+    """Seeded exit waves, object and valid window corners (no GPU output)."""
+    rng = np.random.default_rng(seed)
+    y = (rng.standard_normal((J, N, N)) + 1j * rng.standard_normal((J, N, N))).astype(np.complex64)
+    O = (rng.uniform(0.5, 1.0, (M, M)) * np.exp(1j * rng.uniform(-np.pi, np.pi, (M, M))))
+    O = O.astype(np.complex64)
+    pos = rng.integers(0, M - N + 1, size=(J, 2)).astype(np.int32)
+    return y, O, pos
+
+
+@pytest.mark.parametrize("N,J,M", [(64, 64, 176), (48, 300, 120), (255, 16, 300)])
+def test_matches_oracle_on_two_calls_in_a_row(N, J, M):
+    from oracle import ptycho as optycho
+    alpha = 1e-6
+    for seed in (0, 1):
+        y, O, pos = _synthetic(N, J, M, seed)
+        ref = optycho.concur_probe(y.astype(np.complex128), O.astype(np.complex128), pos, alpha)
+        rc, P = _no_alloc(y, O, pos, alpha)
+        assert rc == native.PTYCHO_OK
+        assert _rel(P, ref) <= TOL, (N, J, seed, _rel(P, ref))
 
 
 def test_rejects_sizes_beyond_the_scratch_and_bad_windows():
