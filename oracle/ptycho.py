@@ -25,6 +25,11 @@ where "max" is the maximum of that denominator over its array and a pixel
 whose regularised denominator is exactly 0 is set to 0.  The result is the
 re-split stack z_j = P * O_j.  Sums over j run in ascending j.
 
+The paper does not say when the probe update begins.  The default reading
+updates the object and then the probe from the first iteration; with
+``probe_start = K`` the concur step of iterations k < K (k counted from 0)
+updates the object only and keeps the probe as it is (the other reading).
+
 One iteration is the displayed general update of the Introduction,
 x_{k+1} = a P^b_C P^c_D x_k + (1 - a) x_k, evaluated by ``abc.abc_step`` with
 the two projections above.  The Fourier error of the divide input,
@@ -112,11 +117,12 @@ class Problem:
 
     ``project_C`` updates the estimate (object sweep, then probe sweep) and
     returns the consensus stack; ``project_D`` records the Fourier error of its
-    input in ``last_error``.
+    input in ``last_error``.  ``iterate`` counts the iterations it has run; in
+    those with index below ``probe_start`` the probe sweep is skipped.
     """
 
     def __init__(self, intensity: np.ndarray, pos: np.ndarray,
-                 O: np.ndarray, P: np.ndarray, alpha: float = 1e-6):
+                 O: np.ndarray, P: np.ndarray, alpha: float = 1e-6, probe_start: int = 0):
         self.I = np.asarray(intensity, dtype=np.float64)
         self.sqrtI = np.sqrt(self.I)
         self.sumI = float(self.I.sum())
@@ -125,6 +131,9 @@ class Problem:
         self.P = np.array(P, dtype=np.complex128)
         self.alpha = float(alpha)
         self.last_error = float("nan")
+        self.probe_start = int(probe_start)
+        self.k = 0                      # iterations run so far
+        self._hold_probe = False
 
     def project_D(self, x: np.ndarray) -> np.ndarray:
         y, err = project_D(x, self.sqrtI)
@@ -133,12 +142,16 @@ class Problem:
 
     def project_C(self, y: np.ndarray) -> np.ndarray:
         self.O = concur_object(y, self.P, self.pos, self.O.shape, self.alpha)
-        self.P = concur_probe(y, self.O, self.pos, self.alpha)
+        if not self._hold_probe:
+            self.P = concur_probe(y, self.O, self.pos, self.alpha)
         return exit_waves(self.P, self.O, self.pos)
 
     def iterate(self, x: np.ndarray, a: float, b: float, c: float) -> np.ndarray:
         """x_{k+1} = a P^b_C P^c_D x_k + (1 - a) x_k."""
-        return _abc.abc_step(x, self.project_D, self.project_C, a, b, c)
+        self._hold_probe = self.k < self.probe_start
+        out = _abc.abc_step(x, self.project_D, self.project_C, a, b, c)
+        self.k += 1
+        return out
 
     def run(self, x: np.ndarray, a: float, b: float, c: float, n: int):
         """n iterations; returns (x_n, [E_F of x_0 .. x_{n-1}])."""
