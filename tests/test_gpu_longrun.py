@@ -1,31 +1,118 @@
-"""Long-run parity: 200 iterations of the tiny scan (64 patterns of 64 x 64,
-blind start, noiseless) for every preset.
+"""Long-run parity: every iteration of a 200-iteration run is checked, not
+only a chaotic endpoint.
 
-DC is not sensitive to rounding: FP64 oracle runs whose start differs by a
-relative 1e-7 (the size of FP32 rounding) end within 2e-4 of each other, so
-the GPU must match the oracle's final model Fourier error and phase-ramp-
-corrected object error within 1e-3 relative.
+Shadowing (every preset, the tiny scan -- 64 patterns of 64 x 64, blind
+start, noiseless -- and a 256 x 256 scan of 12 positions with Poisson
+noise): the FP64 oracle runs its own trajectory from the blind start; its
+state after k iterations (x_k, O_k, P_k), rounded to FP32, is loaded into a
+fresh GPU context (ptycho_set_exit_waves, ptycho_set_object_probe) and both
+sides take one more iteration from that same state.  x_{k+1}, O_{k+1},
+P_{k+1} and E_F(x_k) must agree to relative L2 <= 1e-5 at
+k in {1, 25, 50, 100, 150, 199} (tiny) and {1, 25, 50} (256^2), so the GPU
+is checked on the states that late iterations actually visit.  The oracle's
+inputs all come from the oracle itself.
 
-AR, DR, SF, RAAR and RRR are chaotic on this blind problem: the same 1e-7
-start perturbation of the FP64 oracle changes the 200-iteration errors by
-0.6% (AR) up to more than 100% (RRR), with error curves that separate past
-1e-3 after about 16 iterations.  No FP32 (or reordered FP64) evaluation can
-track one trajectory that long, so for these settings the test checks
-(i) the per-iteration error curve within 1e-3 for the first 10 iterations, and
-(ii) the final errors within three times the spread of an ensemble of FP64
-oracle runs started from rounding-size perturbations of x_0.
+Endpoints: DC is not sensitive to rounding (FP64 runs whose start differs by
+a relative 1e-7 end within 2e-4 of each other), so the GPU's own 200-
+iteration run must match the oracle's final model Fourier error and phase-
+ramp-corrected object error within 1e-3 relative.  AR, DR, SF, RAAR and RRR
+are chaotic on this blind problem (the same perturbation changes the
+200-iteration errors by 0.6 % up to more than 100 %), so their endpoints are
+placed inside an ensemble: the unperturbed FP64 oracle run and 8 runs whose
+x, O and P receive an independent relative perturbation of 1e-6 after every
+iteration, a model of an evaluation that rounds to FP32 at every step (the
+shadowing test measures the GPU's one-iteration deviation from the oracle at
+1e-7 to 3e-6 on these states; 6e-8 per iteration, the FP32 unit roundoff,
+proved too narrow for RRR).  The GPU's final errors must lie within the
+ensemble's range widened by its width (plus 1e-3 relative), and the GPU's
+rank in the ensemble is reported.  The first 10 iterations of every error
+curve must agree to 1e-3.
+
+The oracle runs go to a process pool started with the spawn method (no
+worker is forked from a process that has used the GPU), one BLAS thread per
+worker.
 """
+import concurrent.futures
+import multiprocessing
+import os
+
 import numpy as np
 import pytest
 
 from oracle import metrics, ptycho as optycho
 from paper_2311_11466_gb300 import native, synth
 
-from gpu_cases import gpu_recon, oracle_problem
+from gpu_cases import oracle_problem, rel_l2, small_spec
 
 pytestmark = pytest.mark.gpu
 
 ITERS = 200
+ENSEMBLE = 8
+PRESETS = ["DC", "AR", "DR", "SF", "RAAR", "RRR"]
+SHADOW_TINY = (1, 25, 50, 100, 150, 199)
+SHADOW_256 = (1, 25, 50)
+TOL = 1e-5
+
+
+def _spec(which):
+    if which == "tiny":
+        return synth.named_spec("tiny")
+    return small_spec(256, ny=3, nx=4, photons=1e6)
+
+
+def _oracle_trajectory(which, name, n_iter, keep, eps=0.0, seed=0):
+    """FP64 oracle run from the blind start (with eps > 0: x, O and P
+    perturbed by an independent relative eps after every iteration); the
+    states after each k in keep, the error curve, and the final model Fourier
+    error and object error.  Runs in a pool worker."""
+    scan = synth.make_scan(_spec(which))
+    prob, x = oracle_problem(scan)
+    rng = np.random.default_rng(seed)
+
+    def jiggle(a):
+        return a * (1 + eps * (rng.standard_normal(a.shape) + 1j * rng.standard_normal(a.shape)))
+
+    abc = native.PRESETS[name]
+    states, curve = {}, []
+    for k in range(1, n_iter + 1):
+        x = prob.iterate(x, *abc)
+        curve.append(prob.last_error)
+        if eps > 0:
+            x, prob.O, prob.P = jiggle(x), jiggle(prob.O), jiggle(prob.P)
+        if k in keep:
+            states[k] = (x.copy(), prob.O.copy(), prob.P.copy())
+    z = optycho.exit_waves(prob.P, prob.O, scan.pos)
+    return {"states": states, "curve": np.array(curve),
+            "ef": metrics.fourier_error(z, prob.I),
+            "eo": metrics.object_error(prob.O, scan.obj_true, scan.N)}
+
+
+def _oracle_one_step(which, name, state):
+    """One oracle iteration from (x_k, O_k, P_k): returns x_{k+1}, O_{k+1}, P_{k+1}, E_F(x_k)."""
+    scan = synth.make_scan(_spec(which))
+    x, O, P = state
+    prob = optycho.Problem(scan.intensity.astype(np.float64), scan.pos, O, P)
+    x1 = prob.iterate(x, *native.PRESETS[name])
+    return x1, prob.O, prob.P, prob.last_error
+
+
+@pytest.fixture(scope="module")
+def pool():
+    old = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    for k in old:
+        os.environ[k] = "1"
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    ex = concurrent.futures.ProcessPoolExecutor(
+        max_workers=workers, mp_context=multiprocessing.get_context("spawn"))
+    try:
+        yield ex
+    finally:
+        ex.shutdown()
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,48 +122,80 @@ def _built():
 
 
 @pytest.fixture(scope="module")
-def scan():
-    return synth.make_scan(synth.named_spec("tiny"))
+def tiny():
+    return synth.make_scan(_spec("tiny"))
 
 
-def _oracle(scan, abc, eps=0.0, seed=0):
-    prob, x = oracle_problem(scan)
-    if eps > 0:
-        rng = np.random.default_rng(seed)
-        x = x * (1 + eps * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)))
-    x, errs = prob.run(x, *abc, ITERS)
-    z = optycho.exit_waves(prob.P, prob.O, scan.pos)
-    return (metrics.fourier_error(z, prob.I), metrics.object_error(prob.O, scan.obj_true, scan.N),
-            np.array(errs))
+def _gpu_one_step(scan, name, state):
+    """One GPU iteration from an FP32 copy of the given state, through the C ABI."""
+    x, O, P = state
+    with native.Reconstruction() as r:
+        r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+        r.set_exit_waves(x.astype(np.complex64))
+        r.set_object_probe(O.astype(np.complex64), P.astype(np.complex64))
+        r.iterate(*native.PRESETS[name], 1)
+        x1 = r.exit_waves()
+        O1, P1 = r.object_probe()
+        e = r.errors()
+    return x1, O1, P1, float(e[-1])
 
 
-def _gpu(scan, abc):
-    with gpu_recon(scan) as r:
-        r.iterate(*abc, ITERS)
+@pytest.mark.parametrize("which", ["tiny", "256"])
+@pytest.mark.parametrize("name", PRESETS)
+def test_shadowing_every_stage_of_the_run(pool, which, name):
+    keep = SHADOW_TINY if which == "tiny" else SHADOW_256
+    traj = pool.submit(_oracle_trajectory, which, name, max(keep), keep).result()
+    scan = synth.make_scan(_spec(which))
+    # both sides start each check from the FP32-rounded oracle state
+    states = {k: tuple(a.astype(np.complex64).astype(np.complex128) for a in traj["states"][k])
+              for k in keep}
+    refs = {k: pool.submit(_oracle_one_step, which, name, states[k]) for k in keep}
+    worst = {}
+    for k in keep:
+        x1r, O1r, P1r, efr = refs[k].result()
+        x1, O1, P1, ef = _gpu_one_step(scan, name, states[k])
+        errs = {"x": rel_l2(x1, x1r), "O": rel_l2(O1, O1r), "P": rel_l2(P1, P1r),
+                "E_F": abs(ef - efr) / efr}
+        worst[k] = errs
+        bad = {q: v for q, v in errs.items() if not v <= TOL}
+        assert not bad, (which, name, k, errs)
+    print(which, name, {k: {q: f"{v:.1e}" for q, v in e.items()} for k, e in worst.items()})
+
+
+def _gpu_run(scan, name):
+    with native.Reconstruction() as r:
+        r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+        r.iterate(*native.PRESETS[name], ITERS)
         e = r.errors()
         ef = r.model_error()
         O, _ = r.object_probe()
     return ef, metrics.object_error(O, scan.obj_true, scan.N), e
 
 
-def test_dc_200_iterations(scan):
-    abc = native.PRESETS["DC"]
-    ef_ref, eo_ref, curve_ref = _oracle(scan, abc)
-    ef, eo, curve = _gpu(scan, abc)
-    assert abs(ef - ef_ref) <= 1e-3 * ef_ref, (ef, ef_ref)
-    assert abs(eo - eo_ref) <= 1e-3 * eo_ref, (eo, eo_ref)
-    np.testing.assert_allclose(curve[:100], curve_ref[:100], rtol=1e-3)
+def test_dc_200_iterations(pool, tiny):
+    ref = pool.submit(_oracle_trajectory, "tiny", "DC", ITERS, ()).result()
+    ef, eo, curve = _gpu_run(tiny, "DC")
+    assert abs(ef - ref["ef"]) <= 1e-3 * ref["ef"], (ef, ref["ef"])
+    assert abs(eo - ref["eo"]) <= 1e-3 * ref["eo"], (eo, ref["eo"])
+    np.testing.assert_allclose(curve[:100], ref["curve"][:100], rtol=1e-3)
     assert curve[-1] < 0.1 * curve[0]
 
 
 @pytest.mark.parametrize("name", ["AR", "DR", "SF", "RAAR", "RRR"])
-def test_chaotic_presets_200_iterations(scan, name):
-    abc = native.PRESETS[name]
-    ef_ref, eo_ref, curve_ref = _oracle(scan, abc)
-    ens = [_oracle(scan, abc, eps=1e-7, seed=s) for s in (1, 2, 3)]
-    spread_f = max(abs(e[0] - ef_ref) for e in ens)
-    spread_o = max(abs(e[1] - eo_ref) for e in ens)
-    ef, eo, curve = _gpu(scan, abc)
-    np.testing.assert_allclose(curve[:10], curve_ref[:10], rtol=1e-3)
-    assert abs(ef - ef_ref) <= 3 * spread_f + 1e-3 * ef_ref, (ef, ef_ref, spread_f)
-    assert abs(eo - eo_ref) <= 3 * spread_o + 1e-3 * eo_ref, (eo, eo_ref, spread_o)
+def test_chaotic_presets_inside_the_oracle_ensemble(pool, tiny, name, record_property):
+    futs = [pool.submit(_oracle_trajectory, "tiny", name, ITERS, ())]
+    futs += [pool.submit(_oracle_trajectory, "tiny", name, ITERS, (), 1e-6, s)
+             for s in range(1, ENSEMBLE + 1)]
+    runs = [f.result() for f in futs]
+    ref = runs[0]
+    ef, eo, curve = _gpu_run(tiny, name)
+    np.testing.assert_allclose(curve[:10], ref["curve"][:10], rtol=1e-3)
+    for label, gpu, vals in (("E_F", ef, [r["ef"] for r in runs]),
+                             ("object", eo, [r["eo"] for r in runs])):
+        lo, hi = min(vals), max(vals)
+        width = hi - lo
+        rank = int(np.sum(np.array(vals) < gpu))
+        record_property(f"{name}_{label}_rank_in_ensemble", f"{rank}/{len(vals)}")
+        print(f"{name} {label}: GPU {gpu:.6g}, ensemble [{lo:.6g}, {hi:.6g}], rank {rank}/{len(vals)}")
+        slack = width + 1e-3 * abs(vals[0])
+        assert lo - slack <= gpu <= hi + slack, (name, label, gpu, lo, hi)
