@@ -133,24 +133,28 @@ def _bf16_peak():
     return 1700.0, "fallback (sustained)"
 
 
-def _kernel_hash() -> str:
+def _kernel_hash(design: str = "cluster") -> str:
     h = hashlib.sha256()
-    for f in ("divide.cu", "common.cuh"):
+    for f in ("divide2p.cu" if design == "twopass" else "divide.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2311_11466_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per divide launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "divide_large_traffic.md")
+def _profiled_traffic(N: int, J: int, design: str = "cluster"):
+    """DRAM bytes per divide launch of the 1024 x 256^2 workload from the
+    committed ncu summary of that divide design, if it was taken on the
+    current kernel source (else None; None for any other workload)."""
+    if (N, J) != (256, 1024):
+        return None
+    name = "divide2p_large_traffic.md" if design == "twopass" else "divide_large_traffic.md"
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != _kernel_hash():
+    if not m or not t or m.group(1) != _kernel_hash(design):
         return None
     return float(t.group(1))
 
@@ -321,8 +325,9 @@ def run_batch_mode(args):
     serve.run_batch(rs, settings, args.warmup)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    serve.run_batch(rs, settings, n)
+    groups, ragged = serve.run_batch(rs, settings, n)
     t_batch = time.perf_counter() - t0
+    tuning = [r.tuning() for r in rs]
     for r in rs:
         r.close()
     rs = load()
@@ -339,9 +344,18 @@ def run_batch_mode(args):
     line = {"metric": "position-updates/s, 16 uneven scans", "mode": "batch", "value": units / t_batch,
             "unit": UNIT, "sequential": units / t_seq, "speedup": t_seq / t_batch, "steps": n,
             "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "launch_groups": groups, "contexts_in_groups": ragged,
             "config": {"scans": [{"J": sc.J, "N": sc.N, "M": list(sc.M_shape),
-                                  "geometry": sc.spec.geometry} for sc in scans],
-                       "settings": [names[i % 6] for i in range(len(scans))]}}
+                                  "geometry": sc.spec.geometry,
+                                  "gather_tile": list(t["gather_tile"]),
+                                  "probe_pixels_per_thread": t["probe_pixels_per_thread"],
+                                  "cluster_size": t["cluster_size"]}
+                                 for sc, t in zip(scans, tuning)],
+                       "settings": [names[i % 6] for i in range(len(scans))],
+                       "tuner_measurements": {f"N={sc.N},J={sc.J}": {"gather_ms": t["gather_ms"],
+                                                                    "probe_ms": t["probe_ms"],
+                                                                    "divide128_ms": t["divide128_ms"]}
+                                              for sc, t in zip(scans, tuning)}}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -394,32 +408,248 @@ def run_serve_mode(args):
 
 def run_compare_mode(args):
     """The shape of the paper's comparison (Figs. 6-8): every (a, b, c) setting,
-    a big and a small probe on the same synthetic object and scan, Fourier
-    error per iteration and the final ambiguity-corrected object error."""
+    a big and a small probe on the same synthetic object and scan, under two
+    readings of when the probe update starts (from the first iteration; after
+    `--probe-start` iterations with the probe held), with the Fourier error
+    curve every 10 iterations and the final ambiguity-corrected object error."""
     from paper_2311_11466_gb300 import build as _build, metrics, native, synth
     _build.build()
     iters = args.e2e_iters
     out = {}
-    for label, radius in (("big", 32.0), ("small", 16.0)):
-        spec = synth.ScanSpec(N=128, ny=12, nx=12, step=16, jitter=2, radius=radius,
-                              defocus=0.02 * (16.0 / radius) ** 2, photons=1e6, seed=6)
-        scan = synth.make_scan(spec)
-        rows = {}
-        for name in ["DC", "AR", "DR", "SF", "RAAR", "RRR"]:
-            with native.Reconstruction() as r:
-                r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
-                r.iterate(*native.PRESETS[name], iters)
-                e = r.errors()
-                O, _ = r.object_probe()
-                rows[name] = {"E_F": {str(k): float(e[k - 1]) for k in (1, 10, 50, 100, iters) if k <= iters},
-                              "model_E_F": r.model_error(),
-                              "object_error": metrics.object_error(O, scan.obj_true, scan.N)}
-        out[label] = {"probe_radius": radius, "J": scan.J, "N": scan.N, "M": list(scan.M_shape),
-                      "results": rows}
-    line = {"metric": "error after iterations, every preset, big vs small probe", "mode": "compare",
-            "iterations": iters, "data": "synthetic", "dtype": "f32", "results": out}
+    for start in (0, args.probe_start):
+        for label, radius in (("big", 32.0), ("small", 16.0)):
+            spec = synth.ScanSpec(N=128, ny=12, nx=12, step=16, jitter=2, radius=radius,
+                                  defocus=0.02 * (16.0 / radius) ** 2, photons=1e6, seed=6)
+            scan = synth.make_scan(spec)
+            rows = {}
+            for name in ["DC", "AR", "DR", "SF", "RAAR", "RRR"]:
+                with native.Reconstruction() as r:
+                    r.set_probe_start(start)
+                    r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+                    r.iterate(*native.PRESETS[name], iters)
+                    e = r.errors()
+                    O, _ = r.object_probe()
+                    rows[name] = {"E_F_curve_every_10": [float(e[k]) for k in range(0, iters, 10)] +
+                                                        [float(e[-1])],
+                                  "model_E_F": r.model_error(),
+                                  "object_error": metrics.object_error(O, scan.obj_true, scan.N)}
+            out[f"probe_start_{start}/{label}"] = {"probe_start": start, "probe_radius": radius,
+                                                   "J": scan.J, "N": scan.N,
+                                                   "M": list(scan.M_shape), "results": rows}
+    line = {"metric": "error after iterations, every preset, big vs small probe, two probe-start readings",
+            "mode": "compare", "iterations": iters, "data": "synthetic", "dtype": "f32",
+            "results": out}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, e2e_iters: int,
+                    local: int, ws: int, rank: int, concur: str = "deterministic",
+                    fp32_compare: bool = False, divide: str = "auto", scan=None,
+                    with_e2e: bool = True):
+    """Time `steps` abc iterations of one scan on this rank's GPU (CUDA events on
+    the library's stream, after `warmup` iterations), the dominant kernel's
+    roofline, the clocks during the timed region, and one end-to-end
+    reconstruction through the C ABI from pinned host buffers.  Returns a dict
+    (the `scan` entry is the synthetic scan itself)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2311_11466_gb300 import native, synth
+
+    if scan is None:
+        scan = synth.make_scan(spec)
+    J, N = scan.J, scan.N
+    # one dedicated stream for the library and for the timing events
+    stream = torch.cuda.Stream(device=local)
+    r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=precision,
+                              concur=concur, divide=divide)
+    r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+    design = r.divide_design()
+    abc = native.PRESETS[preset]
+    r.iterate(*abc, warmup)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    native.ptycho_profile_enable(r.h, True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    r.iterate(*abc, steps)
+    t1.record(stream)
+    t1.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clocks = sampler.stop() if rank == 0 else None
+    native.ptycho_profile_enable(r.h, False)
+    div_ms, con_ms, nrec = native.ptycho_profile_read(r.h)
+    ms = max_over_ranks(ms, torch.device("cuda", local))
+    value = replica_throughput(J * steps, ws, ms / 1e3)
+
+    # roofline of the dominant kernel (the divide step)
+    NN = N * N
+    # algorithmic bytes per pixel of the divide kernel: sqrt I (4) and y_k (8)
+    # always; y_{k-1} (8) when b != 1; x_{k-1} read and x_k written (8 + 8) when a != 1
+    a_, b_, _ = abc
+    div_px = 12.0 + (8.0 if b_ != 1.0 else 0.0) + (16.0 if a_ != 1.0 else 0.0)
+    div_bytes = div_px * J * NN
+    div_avg = div_ms / max(nrec, 1) / 1e3
+    if precision == "bf16x3":
+        flops = 96.0 * N ** 3 * J   # four GEMMs of 2 x N x 2N x 6N per exit wave
+        tflops, tkind = _bf16_peak()
+        roof = {"bound": "tensor", "achieved": flops / div_avg / 1e12, "peak": tflops,
+                "unit": "TFLOP/s", "frac": flops / div_avg / 1e12 / tflops, "traffic": None,
+                "kernel": "divide on tensor cores (prologue + 4 BF16x3 DFT GEMMs, tcgen05)",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": div_avg * 1e3,
+                "peak_source": tkind}
+    else:
+        hbm, peak_kind = _peaks()
+        achieved = div_bytes / div_avg / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": _profiled_traffic(N, J, design),
+                "kernel": f"divide, {design} design (fused re-split + FFT + modulus + IFFT)",
+                "algorithmic_bytes_per_launch": div_bytes,
+                "avg_launch_ms": div_avg * 1e3, "peak_source": peak_kind}
+
+    if not with_e2e:
+        r.close()
+        del stream
+        return {"scan": scan, "value": value, "ms": ms, "abc": abc, "div_px": div_px,
+                "roofline": roof, "design": design, "clocks": clocks,
+                "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1),
+                                       "concur": con_ms / max(nrec, 1)}}
+
+    # end to end through the public API with host buffers (pinned)
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    I_h, pos_h = pin(scan.intensity), pin(scan.pos)
+    O_h, P_h = pin(scan.obj0), pin(scan.probe0)
+    O_out = pin(np.empty(scan.M_shape, dtype=np.complex64))
+    P_out = pin(np.empty((N, N), dtype=np.complex64))
+    e2e_iters = max(e2e_iters, 1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    re2e = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=precision,
+                                 divide=divide)
+    re2e.load_scan(pos_h, I_h, O_h, P_h)
+    re2e.iterate(*abc, e2e_iters)
+    native.ptycho_get_object_probe(re2e.h, O_out, P_out)
+    errs = re2e.errors()
+    w1 = time.perf_counter()
+    e2e_s = max_over_ranks(w1 - w0, torch.device("cuda", local))
+    final_model_err = re2e.model_error()
+    re2e.close()
+    h2d = I_h.nbytes + pos_h.nbytes + O_h.nbytes + P_h.nbytes
+    d2h = O_out.nbytes + P_out.nbytes + errs.nbytes
+    e2e = {"value": replica_throughput(J * e2e_iters, ws, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": h2d / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
+           "step": f"one reconstruction = load_scan (host, pinned) + {e2e_iters} {preset} iterations "
+                   f"+ object/probe/error read-back; bytes per iteration",
+           "final_fourier_error": final_model_err,
+           "fourier_error_iter1": float(errs[0]), f"fourier_error_iter{len(errs)}": float(errs[-1])}
+    if fp32_compare and rank == 0:
+        # the FP32 path on the same scan and iteration count, for the error comparison
+        with native.Reconstruction(device=local, stream=stream.cuda_stream) as r32:
+            r32.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+            r32.iterate(*abc, e2e_iters)
+            e32 = r32.errors()
+            m32 = r32.model_error()
+        e2e["fp32_same_scan"] = {"fourier_error_iter1": float(e32[0]),
+                                 f"fourier_error_iter{len(e32)}": float(e32[-1]),
+                                 "final_fourier_error": m32}
+        e2e["rel_diff_vs_fp32"] = {
+            "iter1": abs(float(errs[0]) - float(e32[0])) / float(e32[0]),
+            f"iter{len(e32)}": abs(float(errs[-1]) - float(e32[-1])) / float(e32[-1]),
+            "final_model": abs(final_model_err - m32) / m32}
+    r.close()
+    del stream
+    return {"scan": scan, "value": value, "ms": ms, "abc": abc, "div_px": div_px, "roofline": roof,
+            "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
+            "clocks": clocks, "e2e": e2e, "design": design}
+
+
+def measure_serving(requests: int, rate: float, iters: int, max_active: int = 16,
+                    iters_per_round: int = 10, budget_gb: int = 180):
+    """The serving workload: `requests` blind RAAR(0.9) reconstructions drawn
+    from a pool of 8 synthetic scans (N in {128, 256}, J log-uniform in
+    [100, 4096]), each `iters` iterations.  Four runs of the same requests:
+      saturation: every request submitted at t = 0; continuous batching
+        (max_active in flight) against the same requests back to back, one
+        reconstruction at a time through the context API;
+      at `rate` req/s (Poisson arrivals): continuous batching against the same
+        server admitting one request at a time (sequential FIFO service).
+    Latency is submission to completion (host wall time, queueing included);
+    per-100 is the service time per 100 iterations.  Each request's final model
+    Fourier error is kept, so equal final error can be checked."""
+    import numpy as np
+    from paper_2311_11466_gb300 import native, serve, synth
+    pool = [synth.make_scan(sp) for sp in synth.serving_specs(8)]
+    rng = np.random.default_rng(4)
+    pick = rng.integers(0, len(pool), size=requests)
+    scans = [pool[i] for i in pick]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=requests))
+    arrivals -= arrivals[0]
+    settings = [native.PRESETS["RAAR"]] * len(scans)
+    budget = budget_gb << 30
+    units = sum(sc.J for sc in scans) * iters
+    serve.run_stream(scans[:2], settings[:2], 2, [0.0, 0.0], budget, 2)  # warm the kernels
+
+    def summarise(recs, wall):
+        lat = np.array([r_["latency_s"] for r_ in recs])
+        per100 = np.array([r_["per100_s"] for r_ in recs])
+        return {"value": units / wall, "wall_s": wall,
+                "latency_p50_s": float(np.percentile(lat, 50)),
+                "latency_p99_s": float(np.percentile(lat, 99)),
+                "per100_p50_s": float(np.percentile(per100, 50)),
+                "per100_p99_s": float(np.percentile(per100, 99))}, \
+            np.array([r_["final_error"] for r_ in recs])
+
+    zero = np.zeros(len(scans))
+    sat, fe_sat = summarise(*serve.run_stream(scans, settings, iters, zero, budget, max_active,
+                                              iters_per_round))
+    # the same requests back to back, one reconstruction at a time
+    fe_seq = np.empty(len(scans))
+    t0 = time.perf_counter()
+    for i, sc in enumerate(scans):
+        with native.Reconstruction() as r:
+            r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+            r.iterate(*settings[i], iters)
+            r.object_probe()
+            fe_seq[i] = r.model_error()
+    t_seq = time.perf_counter() - t0
+    at_rate, fe_rate = summarise(*serve.run_stream(scans, settings, iters, arrivals, budget,
+                                                   max_active, iters_per_round))
+    fifo, fe_fifo = summarise(*serve.run_stream(scans, settings, iters, arrivals, budget, 1,
+                                                iters_per_round))
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    return {
+        "metric": "aggregate position-updates/s; p50/p99 latency (s), queueing included",
+        "unit": UNIT, "requests": len(scans), "iterations": iters, "preset": "RAAR(0.9)",
+        "pool": [{"J": sc.J, "N": sc.N, "geometry": sc.spec.geometry} for sc in pool],
+        "max_active": max_active, "iters_per_round": iters_per_round, "budget_gb": budget_gb,
+        "saturation": {"continuous_batching": sat,
+                       "back_to_back": {"value": units / t_seq, "wall_s": t_seq},
+                       "speedup": sat["value"] / (units / t_seq)},
+        f"at_{rate:g}_req_per_s": {"continuous_batching": at_rate, "sequential_fifo": fifo,
+                                   "speedup": at_rate["value"] / fifo["value"]},
+        "final_model_error": {"mean": float(fe_seq.mean()), "max": float(fe_seq.max()),
+                              "max_rel_diff_vs_back_to_back": {
+                                  "saturation": rel(fe_sat, fe_seq), "at_rate": rel(fe_rate, fe_seq),
+                                  "sequential_fifo": rel(fe_fifo, fe_seq)}},
+        "data": "synthetic", "dtype": "f32",
+    }
 
 
 def main():
@@ -433,11 +663,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the cuFFT comparison timing")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tensor-core (bf16x3) and serving sub-results of the default line")
     ap.add_argument("--mode", default="iterate", choices=["iterate", "batch", "serve", "compare"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--preset", default="RAAR", choices=["DC", "AR", "DR", "SF", "RAAR", "RRR"])
     ap.add_argument("--concur", default="deterministic", choices=["deterministic", "atomic"])
+    ap.add_argument("--divide", default="auto", choices=["auto", "cluster", "twopass"])
     ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--probe-start", type=int, default=10,
+                    help="compare mode: the second reading holds the probe for this many iterations")
     ap.add_argument("--rate", type=float, default=20.0)
     args = ap.parse_args()
     if args.mode == "batch":
@@ -454,7 +689,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args, spec)
 
-    import numpy as np
     import torch
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -468,112 +702,19 @@ def main():
         dist.barrier()
     native.lib()
 
-    scan = synth.make_scan(spec)
+    m = measure_iterate(spec, args.precision, args.preset, args.steps, args.warmup, args.e2e_iters,
+                        local, ws, rank, concur=args.concur,
+                        fp32_compare=args.precision == "bf16x3", divide=args.divide)
+    scan, value, ms, abc = m["scan"], m["value"], m["ms"], m["abc"]
     J, N = scan.J, scan.N
-    # one dedicated stream for the library and for the timing events
-    stream = torch.cuda.Stream(device=local)
-    r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision,
-                              concur=args.concur)
-    r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
-    abc = native.PRESETS[args.preset]
-    r.iterate(*abc, args.warmup)
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    native.ptycho_profile_enable(r.h, True)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    r.iterate(*abc, args.steps)
-    t1.record(stream)
-    t1.synchronize()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    clocks = sampler.stop() if rank == 0 else None
-    native.ptycho_profile_enable(r.h, False)
-    div_ms, con_ms, nrec = native.ptycho_profile_read(r.h)
-    ms = max_over_ranks(ms, torch.device("cuda", local))
-    value = replica_throughput(J * args.steps, ws, ms / 1e3)
-
-    # roofline of the dominant kernel (the divide kernel)
     NN = N * N
-    # algorithmic bytes per pixel of the divide kernel: sqrt I (4) and y_k (8)
-    # always; y_{k-1} (8) when b != 1; x_{k-1} read and x_k written (8 + 8) when a != 1
-    a_, b_, _ = abc
-    div_px = 12.0 + (8.0 if b_ != 1.0 else 0.0) + (16.0 if a_ != 1.0 else 0.0)
-    div_bytes = div_px * J * NN
-    div_avg = div_ms / max(nrec, 1) / 1e3
-    hbm, peak_kind = _peaks()
-    achieved = div_bytes / div_avg / 1e9
-    traffic = _profiled_traffic()
-    if args.precision == "bf16x3":
-        flops = 96.0 * N ** 3 * J   # four GEMMs of 2 x N x 2N x 6N per exit wave
-        tflops, tkind = _bf16_peak()
-        roof = {"bound": "tensor", "achieved": flops / div_avg / 1e12, "peak": tflops,
-                "unit": "TFLOP/s", "frac": flops / div_avg / 1e12 / tflops, "traffic": None,
-                "kernel": "divide on tensor cores (prologue + 4 BF16x3 DFT GEMMs, tcgen05)",
-                "algorithmic_flops_per_launch": flops, "avg_launch_ms": div_avg * 1e3,
-                "peak_source": tkind}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "divide (fused re-split + FFT + modulus + IFFT)",
-                "algorithmic_bytes_per_launch": div_bytes,
-                "avg_launch_ms": div_avg * 1e3, "peak_source": peak_kind}
-
-    # end to end through the public API with host buffers (pinned)
-    def pin(a):
-        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    I_h, pos_h = pin(scan.intensity), pin(scan.pos)
-    O_h, P_h = pin(scan.obj0), pin(scan.probe0)
-    O_out = pin(np.empty(scan.M_shape, dtype=np.complex64))
-    P_out = pin(np.empty((N, N), dtype=np.complex64))
-    e2e_iters = max(args.e2e_iters, 1)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    w0 = time.perf_counter()
-    re2e = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=args.precision)
-    re2e.load_scan(pos_h, I_h, O_h, P_h)
-    re2e.iterate(*abc, e2e_iters)
-    native.ptycho_get_object_probe(re2e.h, O_out, P_out)
-    errs = re2e.errors()
-    w1 = time.perf_counter()
-    e2e_s = w1 - w0
-    e2e_s = max_over_ranks(e2e_s, torch.device("cuda", local))
-    final_model_err = re2e.model_error()
-    re2e.close()
-    h2d = I_h.nbytes + pos_h.nbytes + O_h.nbytes + P_h.nbytes
-    d2h = O_out.nbytes + P_out.nbytes + errs.nbytes
-    e2e = {"value": replica_throughput(J * e2e_iters, ws, e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": h2d / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
-           "step": f"one reconstruction = load_scan (host, pinned) + {e2e_iters} RAAR iterations "
-                   f"+ object/probe/error read-back; bytes per iteration",
-           "final_fourier_error": final_model_err,
-           "fourier_error_iter1": float(errs[0]), f"fourier_error_iter{len(errs)}": float(errs[-1])}
-    if args.precision == "bf16x3" and rank == 0:
-        # the FP32 path on the same scan and iteration count, for the error comparison
-        with native.Reconstruction(device=local, stream=stream.cuda_stream) as r32:
-            r32.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
-            r32.iterate(*abc, e2e_iters)
-            e32 = r32.errors()
-            e2e["fp32_same_scan"] = {"fourier_error_iter1": float(e32[0]),
-                                     f"fourier_error_iter{len(e32)}": float(e32[-1]),
-                                     "final_fourier_error": r32.model_error()}
-    r.close()
 
     unfused = None
     if rank == 0 and args.precision == "fp32" and not args.no_compare:
         cm, fft_ms = cufft_divide_ms(scan, abc[2], torch.device("cuda", local))
-        unfused = {"divide_ms": cm, "fft2_ifft2_only_ms": fft_ms, "fused_divide_ms": div_avg * 1e3,
-                   "speedup": cm / (div_avg * 1e3),
+        div_ms = m["roofline"]["avg_launch_ms"]
+        unfused = {"divide_ms": cm, "fft2_ifft2_only_ms": fft_ms, "fused_divide_ms": div_ms,
+                   "speedup": cm / div_ms,
                    "kind": "comparison only: torch.fft (cuFFT) fft2 + modulus + ifft2 + error sum "
                            "on the same workload; the fused kernel also forms x_k"}
 
@@ -588,6 +729,46 @@ def main():
             cpu["one_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1,
                                  "sample": f"same sample, {one['iterations']} iterations, "
                                            f"one BLAS thread"}
+    # both divide designs at 256^2 on the same scan (the default line uses the
+    # one AUTO picks; this races the two)
+    variants = None
+    if ws == 1 and not args.no_extras and args.precision == "fp32" and N == 256:
+        variants = {"default": m["design"]}
+        for design in ("cluster", "twopass"):
+            v = measure_iterate(spec, "fp32", args.preset, 20, 3, 0, local, ws, rank,
+                                divide=design, scan=scan, with_e2e=False)
+            variants[design] = {"value": v["value"], "ms_per_step": v["ms"] / 20,
+                                "divide_ms": v["roofline"]["avg_launch_ms"],
+                                "divide_hbm_frac": v["roofline"]["frac"],
+                                "divide_gbs": v["roofline"]["achieved"],
+                                "traffic": v["roofline"]["traffic"], "steps": 20, "warmup": 3,
+                                "clocks": v["clocks"]}
+    del scan, m["scan"]
+    extra_launches = 2 * KERNELS_PER_ITER * 20 if variants is not None else 0
+
+    # the rest of the metric (tensor-core path; serving) on a single GPU only
+    extras = {}
+    if ws == 1 and not args.no_extras and args.precision == "fp32" and args.workload == "large":
+        steps_tc = 20
+        t = measure_iterate(synth.named_spec("precision"), "bf16x3", "RAAR", steps_tc, 3, 200,
+                            local, ws, rank, fp32_compare=True)
+        extras["bf16x3"] = {
+            "value": t["value"], "unit": UNIT, "steps": steps_tc, "warmup": 3,
+            "ms_per_step": t["ms"] / steps_tc,
+            "config": {"workload": f"precision: J={t['scan'].J}, N={t['scan'].N}, "
+                                   f"M={t['scan'].M_shape[0]}x{t['scan'].M_shape[1]}, RAAR(0.9), "
+                                   "BF16x3 tensor-core DFT, FP32 accumulation"},
+            "roofline": t["roofline"], "kernel_ms_per_step": t["kernel_ms_per_step"],
+            "clocks": t["clocks"], "e2e": t["e2e"],
+            "errors": {"note": "E_F of the tensor-core path and of the FP32 path on the same scan "
+                               "from the same start, at iterations 1 and 200, and the final model "
+                               "error; rel_diff_vs_fp32 gives their relative differences",
+                       **{k: v for k, v in t["e2e"].items() if k.startswith(("fourier", "final", "fp32", "rel"))}},
+        }
+        extra_launches += (KERNELS_PER_ITER + 4) * steps_tc
+        del t
+        torch.cuda.empty_cache()
+        extras["serving"] = measure_serving(args.requests, args.rate, args.e2e_iters)
 
     if rank == 0:
         line = {
@@ -595,12 +776,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "bf16x3 (f32 accumulate)", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: J={J}, N={N}, M={scan.M_shape[0]}x{scan.M_shape[1]}, "
+            "config": {"workload": f"{args.workload}: J={J}, N={N}, "
                                    f"{args.preset} (a,b,c)={tuple(abc)}, {args.precision}, Poisson {spec.photons}",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "l2": "working set 1.3 GB > L2 (no flush needed)"},
-            "roofline": roof,
-            "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
+                       "l2": "working set > L2 (no flush needed)"},
+            "roofline": m["roofline"],
+            "kernel_ms_per_step": m["kernel_ms_per_step"],
             # the survey's FFT rate: 10 N^2 log2(N^2) flops per position-update (a
             # forward and an inverse 2-D FFT at 5 N^2 log2(N^2) each), against the
             # nominal FP32 CUDA-core peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)
@@ -608,15 +789,20 @@ def main():
                          "flops_per_update": 10.0 * NN * math.log2(NN),
                          "of_fp32_nominal_peak": value * 10.0 * NN * math.log2(NN) / 1e12 / FP32_NOMINAL_TFLOPS,
                          "peak_source": "nominal (not measured)"},
-            "per_step_bytes": (div_px + 16.0) * J * NN,
-            "step_hbm_gbs": (div_px + 16.0) * J * NN / (ms / args.steps / 1e3) / 1e9,
+            "per_step_bytes": (m["div_px"] + 16.0) * J * NN,
+            "step_hbm_gbs": (m["div_px"] + 16.0) * J * NN / (ms / args.steps / 1e3) / 1e9,
             "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)) * args.steps,
-            "clocks": clocks,
-            "e2e": e2e,
+            "clocks": m["clocks"],
+            "e2e": m["e2e"],
             "cpu_baseline": cpu,
         }
         if unfused is not None:
             line["unfused_cufft"] = unfused
+        if variants is not None:
+            line["divide_variants"] = variants
+        if extra_launches:
+            line["extra_timed_launches"] = extra_launches
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

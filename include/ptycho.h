@@ -66,17 +66,28 @@ enum { PTYCHO_PREC_FP32 = 0,    /* FP32 shared-memory FFT (default) */
 enum { PTYCHO_CONCUR_DETERMINISTIC = 0,  /* position-tiled gather, fixed order */
        PTYCHO_CONCUR_ATOMIC = 1 };       /* per-position scatter with atomics */
 
+/* Kernel design of the FP32 divide step (Fig. 3(a)); both compute the same
+ * update, within FP32 rounding of each other. */
+enum { PTYCHO_DIVIDE_AUTO = 0,     /* the faster design for the pattern side */
+       PTYCHO_DIVIDE_CLUSTER = 1,  /* one thread-block cluster per exit wave (any N) */
+       PTYCHO_DIVIDE_TWOPASS = 2   /* row and column passes through L2 with no
+                                      clusters and no transpose buffer (N = 256 only;
+                                      other N use the cluster design) */ };
+
 typedef struct {
     int device;      /* CUDA device ordinal */
     int precision;   /* PTYCHO_PREC_* */
     int concur;      /* PTYCHO_CONCUR_* */
     float alpha;     /* denominator regulariser, >= 0 (default 1e-6) */
     void* stream;    /* cudaStream_t to run on, or NULL for a private stream */
+    int divide;      /* PTYCHO_DIVIDE_* (default AUTO; the tensor-core precision
+                        path always pairs with the cluster design) */
 } ptycho_opts;
 
 typedef struct ptycho_ctx ptycho_ctx;
 
-/* Fill *opts with the defaults (device 0, FP32, deterministic, alpha 1e-6). */
+/* Fill *opts with the defaults (device 0, FP32, deterministic, alpha 1e-6,
+ * divide design AUTO). */
 void ptycho_default_opts(ptycho_opts* opts);
 
 /* Create a context on opts->device.  opts may be NULL for the defaults.
@@ -128,6 +139,52 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter);
  * Errors: EINVAL (lam not finite, n_iter < 0, order not a permutation),
  * ESTATE (no scan), ECUDA. */
 int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t n_iter);
+
+/* Hold the probe fixed in the concur step of iterations k < start, k counted
+ * from 0 at the last ptycho_load_scan: those iterations update the object
+ * only (Fig. 3(b), with the probe as known), and the re-split uses the probe
+ * as it is.  start = 0 (the default) updates the object and then the probe
+ * from the first iteration.  The paper does not say when the probe update
+ * begins; this selects the other reading.  The setting stays with the
+ * context across loads.  Errors: EINVAL (start < 0). */
+int ptycho_set_probe_start(ptycho_ctx* ctx, int32_t start);
+
+/* Launch shapes chosen by the library's autotuner (no counterpart in the
+ * paper).  The first iteration of a context whose kind of scan (device, N,
+ * floor(log2 J)) this process has not seen times the candidate launch shapes
+ * of the concur kernels on the context's data and keeps the fastest; at
+ * 128 x 128 the load of such a scan also times two cluster shapes of the
+ * divide kernel.  The choice is cached for every later context of that kind.
+ * Every candidate computes the same sums in the same order, so results are
+ * bit-identical whichever wins. */
+typedef struct {
+    int32_t tuned;          /* 1 once the concur shapes of this context were chosen */
+    int32_t gather_rows;    /* object-gather tile (candidates 16x32, 8x32, 32x32, 8x64) */
+    int32_t gather_cols;
+    int32_t probe_ppt;      /* probe-partial pixels per thread (1 or 2) */
+    float gather_ms[4];     /* measured ms of each gather candidate, in the order above */
+    float probe_ms[2];      /* measured ms with 1 and 2 pixels per thread */
+    int32_t cluster_size;   /* CTAs per exit wave of the cluster divide kernel (0: two-pass) */
+    float divide_ms[2];     /* 128^2: measured ms of clusters of 8 x 128 and 16 x 64 threads */
+} ptycho_tuning_info;
+
+/* Enable (default) or disable the autotuner for this context's later loads
+ * and first iteration; disabled, it uses the cached choice or the defaults
+ * (16 x 32 tiles, 1 pixel per thread, clusters of 8 at 128^2).
+ * Errors: EINVAL. */
+int ptycho_set_tuning(ptycho_ctx* ctx, int enable);
+
+/* The launch shapes of the context's current scan.  Errors: EINVAL, ESTATE. */
+int ptycho_tuning(const ptycho_ctx* ctx, ptycho_tuning_info* out);
+
+/* Pin the launch shapes of the loaded scan -- one of the gather tiles listed
+ * above, 1 or 2 probe pixels per thread, and at 128 x 128 with the cluster
+ * design the cluster size (8 or 16 CTAs per exit wave; 0 keeps the current
+ * one) -- and stop tuning this context, for reproducing a measurement or a
+ * chosen configuration.  The results do not change.  Synchronises.
+ * Errors: EINVAL (not a candidate), ESTATE (no scan), ECUDA. */
+int ptycho_set_launch_shapes(ptycho_ctx* ctx, int32_t gather_rows, int32_t gather_cols,
+                             int32_t probe_ppt, int32_t cluster_size);
 
 /* Copy the current object [M_rows][M_cols][2] and probe [N][N][2] to host
  * buffers (either may be NULL).  Synchronises.  Errors: ESTATE, ECUDA. */
@@ -187,8 +244,9 @@ int ptycho_profile_read(ptycho_ctx* ctx, double* divide_ms, double* concur_ms, i
  *   probe_out  device complex float32 [N][N], written on success only
  *   stream     cudaStream_t to run on (NULL: the default stream)
  * All buffers stay owned by the caller.  Scratch lives in one static
- * __device__ array of 7.5 MiB that every GPU loading the library holds until
- * the process exits; it bounds N to 256.  The first call on a device looks up
+ * __device__ array of 8.25 MiB that every GPU loading the library holds until
+ * the process exits; it bounds N to 256 (every N from 1 to 256 and every
+ * J >= 1 fit).  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress, with the device current),
  * so make that first call before any stream capture.  Every call reuses the
  * same array (the maximum and the status word are cleared at the start of
@@ -210,11 +268,29 @@ int ptycho_probe_update_noalloc(const float* y, const float* obj, const int32_t*
  * Errors: EINVAL (bad device or timeout), ECUDA. */
 int ptycho_check_bounded_wait(int device, uint32_t timeout_ms);
 
+/* Checked build (no counterpart in the paper): libptycho_debug.so is the same
+ * library compiled with device-side checks of object-window bounds, of the
+ * sqrt(I) input and of NaN/Inf in the exit waves, object and probe it writes.
+ * A failed check records a bit (1 window, 2 non-finite output, 4 bad sqrt(I))
+ * and goes on with a safe value; it never traps.  ptycho_debug_build returns
+ * 1 in the checked build and 0 otherwise. */
+int ptycho_debug_build(void);
+
+/* Synchronise device `device`, then read and clear its check bits into
+ * *flags (always 0 in the normal build).  Errors: EINVAL (bad device or
+ * NULL), ECUDA. */
+int ptycho_debug_flags(int device, uint32_t* flags);
+
 /* Bytes of device memory the context holds for its current scan. */
 size_t ptycho_device_bytes(const ptycho_ctx* ctx);
 
-/* Bytes of device memory a scan of this size would need (for admission). */
+/* Bytes of device memory a scan of this size would need (for admission),
+ * with the default (AUTO) divide design. */
 size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, int precision);
+
+/* The divide design a context uses for its current scan (PTYCHO_DIVIDE_CLUSTER
+ * or PTYCHO_DIVIDE_TWOPASS; 0 without a scan). */
+int ptycho_divide_design(const ptycho_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -9,8 +9,11 @@
  *
  * Batch: a fixed set of loaded contexts advanced together; from the second
  * iteration on, one iteration of every context is captured into a single
- * CUDA graph (one branch per context) and replayed, so a round of the whole
- * batch is one graph launch.
+ * CUDA graph and replayed, so a round of the whole batch is one graph launch.
+ * In that graph the FP32 cluster-design contexts of one pattern side run as
+ * one launch group: one divide launch over all their exit waves (a work list
+ * of (scan, wave) items, however uneven the scans) and one launch per concur
+ * kernel over all their scans; other contexts have a branch of their own.
  *
  * Server: a request queue with admission by an HBM budget, continuous
  * batching (requests join the active set between rounds, as memory and slots
@@ -39,10 +42,17 @@ int ptycho_batch_create(ptycho_batch** out, const ptycho_opts* opts);
 int ptycho_batch_add(ptycho_batch* batch, ptycho_ctx* ctx, float a, float b, float c);
 
 /* Advance every context of the batch by n_iter iterations.  The first
- * iteration is launched directly; the others replay one captured graph.
- * Results are those of ptycho_iterate(ctx, a, b, c, n_iter) on each context
- * alone.  Synchronises.  Errors: EINVAL (n_iter < 0), ESTATE (empty), ECUDA. */
+ * iteration (and any in which a context holds its probe fixed) is launched
+ * directly; the others replay one captured graph.  Results are those of
+ * ptycho_iterate(ctx, a, b, c, n_iter) on each context alone, bit for bit
+ * (a launch group may pin its contexts' concur launch shapes to a common
+ * choice, which changes no result).  Synchronises.
+ * Errors: EINVAL (n_iter < 0), ESTATE (empty), ENOMEM, ECUDA. */
 int ptycho_batch_run(ptycho_batch* batch, int32_t n_iter);
+
+/* Launch groups of the last ptycho_batch_run and how many contexts ran in
+ * them (the rest ran as branches of their own).  Errors: EINVAL. */
+int ptycho_batch_groups(const ptycho_batch* batch, int32_t* groups, int32_t* ragged);
 
 /* Release the batch (not its contexts).  NULL is a no-op. */
 void ptycho_batch_destroy(ptycho_batch* batch);

@@ -16,23 +16,34 @@
 // in a fixed order: chunk order, or with many chunks contiguous groups of
 // chunks added in group order).  Maxima use integer atomicMax on the bit patterns of
 // non-negative IEEE values, which is order independent.
+#include <vector>
+
 #include "common.cuh"
+#include "debug.cuh"
 #include "internal.h"
+
+PTYCHO_DEBUG_UNIT(concur)
 
 namespace ptycho {
 namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ float block_max_float(float v, float* scratch) {
+// Block maximum of non-negative doubles as the integer maximum of their bit
+// patterns (the same order; no FP64 arithmetic).  Valid in thread 0.
+__device__ __forceinline__ unsigned long long block_max_bits(unsigned long long v,
+                                                             unsigned long long* scratch) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_down_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) scratch[w] = v;
     __syncthreads();
-    float m = 0.f;
+    unsigned long long m = 0ull;
     if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, scratch[i]);
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = scratch[i] > m ? scratch[i] : m;
     return m;
 }
 
@@ -49,69 +60,110 @@ __device__ __forceinline__ double block_max_double(double v, double* scratch) {
 }
 
 // Object numerator/denominator by position-tiled gather.  One CTA per
-// kObjTileR x kObjTile object tile walks its list of overlapping windows (each
-// entry carries the position index and the window corner, so one load per
-// window); thread i owns column i % kObjTile of rows i / kObjTile + kTRG k.
-constexpr int kTRG = kT / kObjTile;       // rows covered by one sweep of the CTA
-static_assert(kT % kObjTile == 0 && kObjTileR % kTRG == 0, "object tile shape");
+// TR x TC object tile walks its list of overlapping windows (each entry
+// carries the position index and the window corner, so one load per window);
+// thread i owns column i % TC of rows i / TC + (kT / TC) k.  For each pixel the
+// windows covering it are added in ascending position order whatever the tile
+// shape, the numerator in FP32.  The denominator sum_j |P|^2 is carried as an
+// unevaluated pair of FP32 values (s, e) with s + e exact at every step
+// (Knuth's TwoSum: each addition's rounding error is recovered exactly and
+// accumulated in e), and the pair is combined in FP64 once per pixel at the
+// end: its final reduction is in FP64 while the loop runs on the FP32 pipe
+// (FP64 inside the loop stalls it: this part issues FP64 at a small
+// fraction of the FP32 rate).  Every tile shape therefore gives bit-identical
+// results (the shape is a pure launch choice).
 
-__global__ void __launch_bounds__(kT) concur_object_kernel(
-    const float2* __restrict__ y, const float2* __restrict__ P, const int4* __restrict__ tile_win,
-    const int* __restrict__ tile_ptr, int N, int Mr, int Mc,
-    int tiles_c, float2* __restrict__ numO, float* __restrict__ denO, unsigned* __restrict__ maxO) {
-    constexpr int KP = kObjTileR / kTRG;  // pixels per thread
-    __shared__ float scratch[kT / 32];
-    const int tile = blockIdx.x;
+// s + x as s' = fl(s + x) with its exact rounding error added to e (TwoSum).
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+    const float t = __fadd_rn(s, x);
+    const float xp = __fsub_rn(t, s);
+    const float sp = __fsub_rn(t, xp);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, sp), __fsub_rn(x, xp)));
+    s = t;
+}
+
+constexpr int kListStage = 256;  // window-list entries staged in shared memory at a time
+
+template <int TR, int TC>
+__device__ __forceinline__ void gather_body(const ConcurScan& cs, const int tile) {
+    constexpr int TRG = kT / TC;          // rows covered by one sweep of the CTA
+    constexpr int KP = TR / TRG;          // pixels per thread
+    static_assert(kT % TC == 0 && TR % TRG == 0, "object tile shape");
+    __shared__ unsigned long long scratch[kT / 32];
+    const int N = cs.N, Mr = cs.Mr, Mc = cs.Mc;
+    const int tiles_c = cs.cb.tiles_c;
     const int ti = tile / tiles_c, tj = tile % tiles_c;
-    const int tx = threadIdx.x % kObjTile, ty = threadIdx.x / kObjTile;
-    const int mc = tj * kObjTile + tx;
-    const int mr0 = ti * kObjTileR + ty;
+    const int tx = threadIdx.x % TC, ty = threadIdx.x / TC;
+    const int mc = tj * TC + tx;
+    const int mr0 = ti * TR + ty;
+    const float2* __restrict__ y = cs.y;
+    const float2* __restrict__ P = cs.P;
+    const int4* __restrict__ tile_win = cs.cb.tile_win;
     float2 acc[KP];
-    float den[KP];
+    float ds[KP], de[KP];   // denominator: sum and accumulated rounding errors
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
         acc[k] = make_float2(0.f, 0.f);
-        den[k] = 0.f;
+        ds[k] = 0.f;
+        de[k] = 0.f;
     }
     const size_t NN = (size_t)N * N;
-    const int l0 = tile_ptr[tile], l1 = tile_ptr[tile + 1];
-    // deep unrolling keeps several windows' loads in flight per thread
+    const int l0 = cs.cb.tile_ptr[tile], l1 = cs.cb.tile_ptr[tile + 1];
+    // The tile's window list is staged in shared memory (kListStage entries at
+    // a time), so the loads of y and P depend on a shared-memory load rather
+    // than on a global one; deep unrolling keeps several windows in flight.
+    __shared__ int4 list[kListStage];
+    for (int b0 = l0; b0 < l1; b0 += kListStage) {
+    const int nb = min(kListStage, l1 - b0);
+    __syncthreads();  // the previous batch is consumed
+    for (int i = threadIdx.x; i < nb; i += kT) list[i] = __ldg(tile_win + b0 + i);
+    __syncthreads();
 #pragma unroll(KP >= 8 ? 1 : 8 / KP)
-    for (int l = l0; l < l1; ++l) {
-        const int4 w = __ldg(tile_win + l);  // (position j, row, col) of the window
+    for (int l = 0; l < nb; ++l) {
+        const int4 w = list[l];  // (position j, row, col) of the window
+#if PT_DBG_ENABLED
+        // checked build: an entry whose window leaves the object is recorded and skipped
+        if (w.x < 0 || w.y < 0 || w.z < 0 || w.y > Mr - N || w.z > Mc - N) {
+            if (threadIdx.x == 0) PT_DBG_FLAG(kDbgWindow);
+            continue;
+        }
+#endif
         const int cc = mc - w.z;
         const bool cin = (unsigned)cc < (unsigned)N;
         const float2* yj = y + (size_t)w.x * NN;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            const int rr = mr0 + kTRG * k - w.y;
+            const int rr = mr0 + TRG * k - w.y;
             if (cin && (unsigned)rr < (unsigned)N) {
                 const int o = rr * N + cc;
                 const float2 pv = __ldg(P + o);
                 const float2 yv = __ldcs(yj + o);
                 acc[k] = cadd(acc[k], cconjmul(pv, yv));
-                den[k] += cabs2(pv);
+                two_sum_acc(ds[k], de[k], cabs2(pv));
             }
         }
     }
-    float mx = 0.f;
+    }
+    unsigned long long mx = 0ull;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
-        const int mr = mr0 + kTRG * k;
+        const int mr = mr0 + TRG * k;
         if (mr < Mr && mc < Mc) {
-            numO[(size_t)mr * Mc + mc] = acc[k];
-            denO[(size_t)mr * Mc + mc] = den[k];
-            mx = fmaxf(mx, den[k]);
+            const double den = (double)ds[k] + (double)de[k];   // the final reduction, FP64
+            cs.cb.numO[(size_t)mr * Mc + mc] = acc[k];
+            cs.cb.denO[(size_t)mr * Mc + mc] = den;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(den);
+            mx = b > mx ? b : mx;
         }
     }
-    const float bm = block_max_float(mx, scratch);
-    if (threadIdx.x == 0) atomicMax(maxO, __float_as_uint(bm));
+    const unsigned long long bm = block_max_bits(mx, scratch);
+    if (threadIdx.x == 0) atomicMax(cs.cb.maxO, bm);
 }
 
 // Atomic variant: one CTA row per (position, 256 probe pixels), scatter-add.
 __global__ void __launch_bounds__(kT) scatter_object_kernel(
     const float2* __restrict__ y, const float2* __restrict__ P, const int2* __restrict__ pos,
-    int N, int Mc, float2* __restrict__ numO, float* __restrict__ denO) {
+    int N, int Mc, float2* __restrict__ numO, double* __restrict__ denO) {
     const int j = blockIdx.y;
     const int r = blockIdx.x * kT + threadIdx.x;
     if (r >= N * N) return;
@@ -121,54 +173,105 @@ __global__ void __launch_bounds__(kT) scatter_object_kernel(
     const float2 yv = __ldcs(y + (size_t)j * N * N + r);
     const size_t m = (size_t)(s.x + rr) * Mc + s.y + cc;
     atomicAdd(numO + m, cconjmul(pv, yv));
-    atomicAdd(denO + m, cabs2(pv));
+    atomicAdd(denO + m, (double)cabs2(pv));
 }
 
-__global__ void __launch_bounds__(kT) max_float_kernel(const float* __restrict__ v, size_t n,
-                                                       unsigned* __restrict__ out) {
-    __shared__ float scratch[kT / 32];
-    float m = 0.f;
+__global__ void __launch_bounds__(kT) max_double_kernel(const double* __restrict__ v, size_t n,
+                                                        unsigned long long* __restrict__ out) {
+    __shared__ double scratch[kT / 32];
+    double m = 0.0;
     for (size_t i = blockIdx.x * (size_t)kT + threadIdx.x; i < n; i += (size_t)gridDim.x * kT)
-        m = fmaxf(m, v[i]);
-    const float bm = block_max_float(m, scratch);
-    if (threadIdx.x == 0) atomicMax(out, __float_as_uint(bm));
+        m = fmax(m, v[i]);
+    const double bm = block_max_double(m, scratch);
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(bm));
 }
 
-__global__ void __launch_bounds__(kT) object_normalise_kernel(
-    const float2* __restrict__ numO, const float* __restrict__ denO,
-    const unsigned* __restrict__ maxO, size_t M, float alpha, float2* __restrict__ O,
-    unsigned long long* __restrict__ maxP) {
-    const size_t m = blockIdx.x * (size_t)kT + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *maxP = 0ull;  // the probe sweep comes next
+// O = num / (den + alpha max(den)): the regularised denominator in FP64,
+// rounded once to FP32 for the division of the FP32 numerator.  Block 0 also
+// clears the probe maximum for the probe sweep that comes next.
+__device__ __forceinline__ void onorm_body(const ConcurScan& cs, const int block) {
+    const size_t M = (size_t)cs.Mr * cs.Mc;
+    const size_t m = block * (size_t)kT + threadIdx.x;
+    if (block == 0 && threadIdx.x == 0) *cs.cb.maxP = 0ull;
     if (m >= M) return;
-    const float mx = __uint_as_float(*maxO);
-    const float d = denO[m] + alpha * mx;
-    const float2 nv = numO[m];
-    O[m] = d > 0.f ? make_float2(nv.x / d, nv.y / d) : make_float2(0.f, 0.f);
+    const double am = cs.alpha * __longlong_as_double((long long)*cs.cb.maxO);
+    const float d = (float)(cs.cb.denO[m] + am);
+    const float2 nv = cs.cb.numO[m];
+    const float2 o = d > 0.f ? make_float2(nv.x / d, nv.y / d) : make_float2(0.f, 0.f);
+    cs.O[m] = o;
+#if PT_DBG_ENABLED
+    if (PT_DBG_NONFINITE2(o)) PT_DBG_FLAG(kDbgNonFinite);
+#endif
 }
 
-// Probe partial sums over a chunk of positions; thread = one probe pixel.
-__global__ void __launch_bounds__(kT) probe_partial_kernel(
-    const float2* __restrict__ y, const float2* __restrict__ O, const int2* __restrict__ pos,
-    int J, int N, int Mc, int chunks, float2* __restrict__ partP, float* __restrict__ partPd) {
-    const int r = blockIdx.x * kT + threadIdx.x;
-    const int ch = blockIdx.y;
-    if (r >= N * N) return;
-    const int rr = r / N, cc = r % N;
+// Probe partial sums over a chunk of positions; thread = PPT adjacent probe
+// pixels (PPT = 2: y read with 16-byte loads).  Each pixel adds its chunk's
+// positions in ascending order with the same operations for either PPT, so
+// both give bit-identical partials (a pure launch choice).
+template <int PPT>
+__device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, const int ch) {
+    static_assert(PPT == 1 || PPT == 2, "pixels per thread");
+    const int N = cs.N, Mc = cs.Mc, J = cs.J, chunks = cs.cb.chunks;
+    const int r = (bx * kT + threadIdx.x) * PPT;
+    // N is even, so with PPT = 2 both pixels of a thread are inside or both out;
+    // threads past the last pixel still take part in the staging below
+    const int rr = r < N * N ? r / N : 0, cc = r < N * N ? r % N : 0;
     const int j0 = (int)(((long)ch * J) / chunks), j1 = (int)(((long)(ch + 1) * J) / chunks);
     const size_t NN = (size_t)N * N;
-    float2 acc = make_float2(0.f, 0.f);
-    float den = 0.f;
-#pragma unroll 4
-    for (int j = j0; j < j1; ++j) {
-        const int2 s = pos[j];
-        const float2 ov = __ldg(O + (size_t)(s.x + rr) * Mc + s.y + cc);
-        const float2 yv = __ldcs(y + (size_t)j * NN + r);
-        acc = cadd(acc, cconjmul(ov, yv));
-        den += cabs2(ov);
+    const float2* __restrict__ y = cs.y;
+    const float2* __restrict__ O = cs.O;
+    const int2* __restrict__ pos = cs.pos;
+    float2 acc[PPT];
+    float den[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        acc[i] = make_float2(0.f, 0.f);
+        den[i] = 0.f;
     }
-    partP[(size_t)ch * NN + r] = acc;
-    partPd[(size_t)ch * NN + r] = den;
+    // the chunk's positions staged in shared memory (every thread of the block
+    // takes part in the staging, including those past the last pixel)
+    __shared__ int2 spos[kListStage];
+    for (int b0 = j0; b0 < j1; b0 += kListStage) {
+    const int nb = min(kListStage, j1 - b0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += kT) spos[i] = pos[b0 + i];
+    __syncthreads();
+    if (r < N * N) {
+#pragma unroll 4
+    for (int jj = 0; jj < nb; ++jj) {
+        const int j = b0 + jj;
+        const int2 s = spos[jj];
+#if PT_DBG_ENABLED
+        // checked build: a window outside the object is recorded and skipped
+        if (s.x < 0 || s.y < 0 || s.x > cs.Mr - N || s.y > Mc - N) {
+            PT_DBG_FLAG(kDbgWindow);
+            continue;
+        }
+#endif
+        const float2* op = O + (size_t)(s.x + rr) * Mc + s.y + cc;
+        float2 yv[PPT];
+        if constexpr (PPT == 2) {
+            const float4 f = __ldcs(reinterpret_cast<const float4*>(y + (size_t)j * NN + r));
+            yv[0] = make_float2(f.x, f.y);
+            yv[1] = make_float2(f.z, f.w);
+        } else {
+            yv[0] = __ldcs(y + (size_t)j * NN + r);
+        }
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const float2 ov = __ldg(op + i);
+            acc[i] = cadd(acc[i], cconjmul(ov, yv[i]));
+            den[i] += cabs2(ov);
+        }
+    }
+    }
+    }
+    if (r >= N * N) return;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        cs.cb.partP[(size_t)ch * NN + r + i] = acc[i];
+        cs.cb.partPd[(size_t)ch * NN + r + i] = den[i];
+    }
 }
 
 // FP64 totals of the probe partials: a block takes kT / RG probe pixels, its
@@ -178,31 +281,32 @@ __global__ void __launch_bounds__(kT) probe_partial_kernel(
 // add the per-CTA Fourier-error partials of the divide step in fixed slices,
 // one FP64 slice total per block, so the final sum (in the normalise kernel)
 // is over one value per block.
+constexpr int kManyChunks = 8;  // above this the chunks are added by 8 thread groups
+
 template <int RG>
-__global__ void __launch_bounds__(kT) probe_reduce_kernel(
-    const float2* __restrict__ partP, const float* __restrict__ partPd, int NN, int chunks,
-    double2* __restrict__ numP, double* __restrict__ denP, unsigned long long* __restrict__ maxP,
-    const double* __restrict__ e_part, int n_part, double* __restrict__ e_slice) {
+__device__ __forceinline__ void preduce_body(const ConcurScan& cs, const int block,
+                                             const int n_blocks) {
     constexpr int RP = kT / RG;
     __shared__ double gx[RG][RP], gy[RG][RP], gd[RG][RP];
     __shared__ double scratch_s[kT / 32], scratch_m[kT / 32];
+    const int NN = cs.N * cs.N, chunks = cs.cb.chunks;
     const int px = threadIdx.x % RP, grp = threadIdx.x / RP;
-    const int r = blockIdx.x * RP + px;
+    const int r = block * RP + px;
     const int c0 = (grp * chunks) / RG, c1 = ((grp + 1) * chunks) / RG;
     double nx = 0.0, ny = 0.0, d = 0.0;
     if (r < NN) {
         for (int ch = c0; ch < c1; ++ch) {
-            const float2 p = partP[(size_t)ch * NN + r];
+            const float2 p = cs.cb.partP[(size_t)ch * NN + r];
             nx += (double)p.x;
             ny += (double)p.y;
-            d += (double)partPd[(size_t)ch * NN + r];
+            d += (double)cs.cb.partPd[(size_t)ch * NN + r];
         }
     }
     double mx = 0.0;
     if constexpr (RG == 1) {
         if (r < NN) {
-            numP[r] = make_double2(nx, ny);
-            denP[r] = d;
+            cs.cb.numP[r] = make_double2(nx, ny);
+            cs.cb.denP[r] = d;
             mx = d;
         }
     } else {
@@ -218,50 +322,116 @@ __global__ void __launch_bounds__(kT) probe_reduce_kernel(
                 ty += gy[g][px];
                 td += gd[g][px];
             }
-            numP[r] = make_double2(tx, ty);
-            denP[r] = td;
+            cs.cb.numP[r] = make_double2(tx, ty);
+            cs.cb.denP[r] = td;
             mx = td;
         }
     }
-    const int per = (n_part + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int e0 = (int)blockIdx.x * per, e1 = min(n_part, e0 + per);
+    const int n_part = cs.n_part;
+    const int per = (n_part + n_blocks - 1) / n_blocks;
+    const int e0 = block * per, e1 = min(n_part, e0 + per);
     double es = 0.0;
-    for (int i = e0 + (int)threadIdx.x; i < e1; i += kT) es += e_part[i];
+    for (int i = e0 + (int)threadIdx.x; i < e1; i += kT) es += cs.e_part[i];
     const double slice = block_sum_double<kT>(es, scratch_s);
-    if (threadIdx.x == 0) e_slice[blockIdx.x] = slice;
+    if (threadIdx.x == 0) cs.cb.e_slice[block] = slice;
     const double bm = block_max_double(mx, scratch_m);
-    if (threadIdx.x == 0) atomicMax(maxP, (unsigned long long)__double_as_longlong(bm));
+    if (threadIdx.x == 0) atomicMax(cs.cb.maxP, (unsigned long long)__double_as_longlong(bm));
 }
-
-constexpr int kManyChunks = 8;  // above this the chunks are added by 8 thread groups
 
 // Probe update, plus (block 0) the iteration's Fourier error, stored in the
 // ring at the slot of the device-side iteration counter (so a captured graph
 // replays correctly), and the reset of the object maximum.
-__global__ void __launch_bounds__(kT) probe_normalise_kernel(
-    const double2* __restrict__ numP, const double* __restrict__ denP,
-    const unsigned long long* __restrict__ maxP, int NN, double alpha, float2* __restrict__ P,
-    const double* __restrict__ e_slice, int n_slice, double inv_sumI, double* __restrict__ e_ring,
-    unsigned long long* __restrict__ d_iter, int ring_cap, unsigned* __restrict__ maxO) {
+__device__ __forceinline__ void pnorm_body(const ConcurScan& cs, const int block, const int n_slice) {
     __shared__ double scratch[kT / 32];
-    const int r = blockIdx.x * kT + threadIdx.x;
+    const int NN = cs.N * cs.N;
+    const int r = block * kT + threadIdx.x;
     if (r < NN) {
-        const double mx = __longlong_as_double((long long)*maxP);
-        const double d = denP[r] + alpha * mx;
-        const double2 nv = numP[r];
-        P[r] = d > 0.0 ? make_float2((float)(nv.x / d), (float)(nv.y / d)) : make_float2(0.f, 0.f);
+        const double mx = __longlong_as_double((long long)*cs.cb.maxP);
+        const double d = cs.cb.denP[r] + cs.alpha * mx;
+        const double2 nv = cs.cb.numP[r];
+        const float2 p = d > 0.0 ? make_float2((float)(nv.x / d), (float)(nv.y / d)) : make_float2(0.f, 0.f);
+        cs.P[r] = p;
+#if PT_DBG_ENABLED
+        if (PT_DBG_NONFINITE2(p)) PT_DBG_FLAG(kDbgNonFinite);
+#endif
     }
-    if (blockIdx.x == 0) {
+    if (block == 0) {
         double s = 0.0;
-        for (int i = threadIdx.x; i < n_slice; i += kT) s += e_slice[i];
+        for (int i = threadIdx.x; i < n_slice; i += kT) s += cs.cb.e_slice[i];
         const double tot = block_sum_double<kT>(s, scratch);
         if (threadIdx.x == 0) {
-            const unsigned long long k = *d_iter;
-            e_ring[k % (unsigned long long)ring_cap] = tot * inv_sumI;
-            *d_iter = k + 1;
-            *maxO = 0u;
+            const unsigned long long k = *cs.d_iter;
+            cs.e_ring[k % (unsigned long long)cs.ring_cap] = tot * cs.inv_sumI;
+            *cs.d_iter = k + 1;
+            *cs.cb.maxO = 0ull;
         }
     }
+}
+
+// ---- one scan per launch -----------------------------------------------------
+template <int TR, int TC>
+__global__ void __launch_bounds__(kT) concur_object_kernel(const ConcurScan cs) {
+    gather_body<TR, TC>(cs, blockIdx.x);
+}
+__global__ void __launch_bounds__(kT) object_normalise_kernel(const ConcurScan cs) {
+    onorm_body(cs, blockIdx.x);
+}
+template <int PPT>
+__global__ void __launch_bounds__(kT) probe_partial_kernel(const ConcurScan cs) {
+    ppart_body<PPT>(cs, blockIdx.x, blockIdx.y);
+}
+template <int RG>
+__global__ void __launch_bounds__(kT) probe_reduce_kernel(const ConcurScan cs) {
+    preduce_body<RG>(cs, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kT) probe_normalise_kernel(const ConcurScan cs, int n_slice) {
+    pnorm_body(cs, blockIdx.x, n_slice);
+}
+
+// ---- several scans per launch (batching) ---------------------------------------
+// first[s] is the first block of scan s in this launch's numbering; every block
+// runs the single-scan work with its scan's arguments, so each scan's results
+// are those of its own launches.
+__device__ __forceinline__ int find_scan(const int* __restrict__ first, int n, int b) {
+    int s = 0;
+    while (s + 1 < n && first[s + 1] <= b) ++s;
+    return s;
+}
+template <int TR, int TC>
+__global__ void __launch_bounds__(kT) ragged_gather_kernel(const ConcurScan* __restrict__ scans,
+                                                           const int* __restrict__ first, int n) {
+    const int s = find_scan(first, n, blockIdx.x);
+    gather_body<TR, TC>(scans[s], blockIdx.x - first[s]);
+}
+__global__ void __launch_bounds__(kT) ragged_onorm_kernel(const ConcurScan* __restrict__ scans,
+                                                          const int* __restrict__ first, int n) {
+    const int s = find_scan(first, n, blockIdx.x);
+    onorm_body(scans[s], blockIdx.x - first[s]);
+}
+template <int PPT>
+__global__ void __launch_bounds__(kT) ragged_ppart_kernel(const ConcurScan* __restrict__ scans,
+                                                          const int* __restrict__ first, int n) {
+    const int s = find_scan(first, n, blockIdx.x);
+    const ConcurScan& cs = scans[s];
+    const int b = blockIdx.x - first[s];
+    const int per_chunk = (cs.N * cs.N / PPT + kT - 1) / kT;
+    ppart_body<PPT>(cs, b % per_chunk, b / per_chunk);
+}
+__global__ void __launch_bounds__(kT) ragged_preduce_kernel(const ConcurScan* __restrict__ scans,
+                                                            const int* __restrict__ first, int n) {
+    const int s = find_scan(first, n, blockIdx.x);
+    const ConcurScan& cs = scans[s];
+    const int nb = first[s + 1] - first[s];
+    if (cs.cb.chunks > kManyChunks)
+        preduce_body<8>(cs, blockIdx.x - first[s], nb);
+    else
+        preduce_body<1>(cs, blockIdx.x - first[s], nb);
+}
+__global__ void __launch_bounds__(kT) ragged_pnorm_kernel(const ConcurScan* __restrict__ scans,
+                                                          const int* __restrict__ first,
+                                                          const int* __restrict__ n_slice, int n) {
+    const int s = find_scan(first, n, blockIdx.x);
+    pnorm_body(scans[s], blockIdx.x - first[s], n_slice[s]);
 }
 
 __global__ void __launch_bounds__(kT) sum_parts_kernel(const double* __restrict__ parts, int n,
@@ -323,6 +493,47 @@ __global__ void __launch_bounds__(kT) materialise_kernel(float2* __restrict__ x,
 
 }  // namespace
 
+void build_tile_csr(const int32_t* pos_rc, int J, int N, int Mr, int Mc, TileShape sh,
+                    std::vector<int>& ptr, std::vector<int4>& list) {
+    const int tr = (Mr + sh.rows - 1) / sh.rows, tc = (Mc + sh.cols - 1) / sh.cols;
+    ptr.assign((size_t)tr * tc + 1, 0);
+    for (int j = 0; j < J; ++j) {
+        const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+        for (int ti = r / sh.rows; ti <= (r + N - 1) / sh.rows; ++ti)
+            for (int tj = c / sh.cols; tj <= (c + N - 1) / sh.cols; ++tj) ptr[(size_t)ti * tc + tj + 1]++;
+    }
+    for (size_t t = 1; t < ptr.size(); ++t) ptr[t] += ptr[t - 1];
+    list.resize((size_t)ptr.back());
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int j = 0; j < J; ++j) {
+        const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+        for (int ti = r / sh.rows; ti <= (r + N - 1) / sh.rows; ++ti)
+            for (int tj = c / sh.cols; tj <= (c + N - 1) / sh.cols; ++tj)
+                list[(size_t)fill[(size_t)ti * tc + tj]++] = make_int4(j, r, c, 0);
+    }
+}
+
+size_t tile_csr_ptr_bound(int N, int Mr, int Mc) {
+    (void)N;
+    size_t m = 0;
+    for (const TileShape& sh : kGatherShape) {
+        const size_t t = (size_t)((Mr + sh.rows - 1) / sh.rows) * ((Mc + sh.cols - 1) / sh.cols) + 1;
+        m = t > m ? t : m;
+    }
+    return m;
+}
+
+size_t tile_csr_entries_bound(int J, int N) {
+    size_t m = 0;
+    for (const TileShape& sh : kGatherShape) {
+        // a window of side N touches at most ceil(N / s) + 1 tiles of side s along
+        // each axis (one more than it fills when it straddles a tile boundary)
+        const size_t t = (size_t)((N + sh.rows - 1) / sh.rows + 1) * ((N + sh.cols - 1) / sh.cols + 1);
+        m = t > m ? t : m;
+    }
+    return (size_t)J * m;
+}
+
 int probe_reduce_blocks(int N, int chunks) {
     const int rp = chunks > kManyChunks ? kT / 8 : kT;
     return (N * N + rp - 1) / rp;
@@ -336,39 +547,98 @@ int probe_chunks(int J, int N) {
     return ch;
 }
 
-cudaError_t launch_concur(const float2* y, float2* P, float2* O, const int2* pos,
-                          const ConcurBufs& cb, int J, int N, int Mr, int Mc, float alpha,
-                          const double* e_part, int n_part, double inv_sumI, double* e_ring,
-                          unsigned long long* d_iter, int ring_cap, int concur_mode,
-                          cudaStream_t st) {
-    const size_t M = (size_t)Mr * Mc;
-    const int NN = N * N;
+cudaError_t launch_gather(const ConcurScan& cs, cudaStream_t st) {
+    const unsigned grid = (unsigned)(cs.cb.tiles_r * cs.cb.tiles_c);
+    switch (cs.cb.gather_shape) {
+        case 0: concur_object_kernel<16, 32><<<grid, kT, 0, st>>>(cs); break;
+        case 1: concur_object_kernel<8, 32><<<grid, kT, 0, st>>>(cs); break;
+        case 2: concur_object_kernel<32, 32><<<grid, kT, 0, st>>>(cs); break;
+        case 3: concur_object_kernel<8, 64><<<grid, kT, 0, st>>>(cs); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_partial(const ConcurScan& cs, cudaStream_t st) {
+    const int NN = cs.N * cs.N;
+    if (cs.cb.probe_ppt == 2)
+        probe_partial_kernel<2><<<dim3((NN / 2 + kT - 1) / kT, cs.cb.chunks), kT, 0, st>>>(cs);
+    else
+        probe_partial_kernel<1><<<dim3((NN + kT - 1) / kT, cs.cb.chunks), kT, 0, st>>>(cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_probe, cudaStream_t st) {
+    const size_t M = (size_t)cs.Mr * cs.Mc;
+    const int NN = cs.N * cs.N;
+    const ConcurBufs& cb = cs.cb;
     if (concur_mode == 0) {
-        concur_object_kernel<<<cb.tiles_r * cb.tiles_c, kT, 0, st>>>(
-            y, P, cb.tile_win, cb.tile_ptr, N, Mr, Mc, cb.tiles_c, cb.numO, cb.denO, cb.maxO);
+        cudaError_t e = launch_gather(cs, st);
+        if (e != cudaSuccess) return e;
     } else {
         cudaMemsetAsync(cb.numO, 0, M * sizeof(float2), st);
-        cudaMemsetAsync(cb.denO, 0, M * sizeof(float), st);
-        scatter_object_kernel<<<dim3((NN + kT - 1) / kT, J), kT, 0, st>>>(y, P, pos, N, Mc,
-                                                                         cb.numO, cb.denO);
-        max_float_kernel<<<304, kT, 0, st>>>(cb.denO, M, cb.maxO);
+        cudaMemsetAsync(cb.denO, 0, M * sizeof(double), st);
+        scatter_object_kernel<<<dim3((NN + kT - 1) / kT, cs.J), kT, 0, st>>>(cs.y, cs.P, cs.pos, cs.N,
+                                                                            cs.Mc, cb.numO, cb.denO);
+        max_double_kernel<<<304, kT, 0, st>>>(cb.denO, M, cb.maxO);
     }
-    object_normalise_kernel<<<(unsigned)((M + kT - 1) / kT), kT, 0, st>>>(cb.numO, cb.denO,
-                                                                         cb.maxO, M, alpha, O,
-                                                                         cb.maxP);
-    probe_partial_kernel<<<dim3((NN + kT - 1) / kT, cb.chunks), kT, 0, st>>>(
-        y, O, pos, J, N, Mc, cb.chunks, cb.partP, cb.partPd);
-    const int n_slice = probe_reduce_blocks(N, cb.chunks);
+    object_normalise_kernel<<<(unsigned)((M + kT - 1) / kT), kT, 0, st>>>(cs);
+    if (!update_probe) {
+        // the probe is held: the iteration's Fourier error from the divide
+        // kernel's partials, and the object maximum cleared for the next gather
+        record_error_kernel<<<1, kT, 0, st>>>(cs.e_part, cs.n_part, cs.inv_sumI, cs.e_ring,
+                                              cs.d_iter, cs.ring_cap);
+        cudaMemsetAsync(cb.maxO, 0, sizeof(unsigned long long), st);
+        return cudaGetLastError();
+    }
+    {
+        cudaError_t e = launch_probe_partial(cs, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int n_slice = probe_reduce_blocks(cs.N, cb.chunks);
     if (cb.chunks > kManyChunks)
-        probe_reduce_kernel<8><<<n_slice, kT, 0, st>>>(cb.partP, cb.partPd, NN, cb.chunks, cb.numP,
-                                                       cb.denP, cb.maxP, e_part, n_part, cb.e_slice);
+        probe_reduce_kernel<8><<<n_slice, kT, 0, st>>>(cs);
     else
-        probe_reduce_kernel<1><<<n_slice, kT, 0, st>>>(cb.partP, cb.partPd, NN, cb.chunks, cb.numP,
-                                                       cb.denP, cb.maxP, e_part, n_part, cb.e_slice);
-    probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cb.numP, cb.denP, cb.maxP, NN,
-                                                             (double)alpha, P, cb.e_slice, n_slice,
-                                                             inv_sumI, e_ring, d_iter, ring_cap,
-                                                             cb.maxO);
+        probe_reduce_kernel<1><<<n_slice, kT, 0, st>>>(cs);
+    probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cs, n_slice);
+    return cudaGetLastError();
+}
+
+void ragged_concur_tables(const ConcurScan* scans, int n, std::vector<int>& first,
+                          std::vector<int>& n_slice, int totals[5]) {
+    first.assign(5 * (size_t)(n + 1), 0);
+    n_slice.assign((size_t)n, 0);
+    for (int s = 0; s < n; ++s) {
+        const ConcurScan& cs = scans[s];
+        const int NN = cs.N * cs.N;
+        const size_t M = (size_t)cs.Mr * cs.Mc;
+        n_slice[s] = probe_reduce_blocks(cs.N, cs.cb.chunks);
+        const int blocks[5] = {cs.cb.tiles_r * cs.cb.tiles_c, (int)((M + kT - 1) / kT),
+                               ((NN / cs.cb.probe_ppt + kT - 1) / kT) * cs.cb.chunks, n_slice[s],
+                               (NN + kT - 1) / kT};
+        for (int k = 0; k < 5; ++k)
+            first[(size_t)k * (n + 1) + s + 1] = first[(size_t)k * (n + 1) + s] + blocks[k];
+    }
+    for (int k = 0; k < 5; ++k) totals[k] = first[(size_t)k * (n + 1) + n];
+}
+
+cudaError_t launch_concur_ragged(const RaggedConcur& rc, cudaStream_t st) {
+    const int n = rc.n;
+    const int* f = rc.first;
+    switch (rc.gather_shape) {
+        case 0: ragged_gather_kernel<16, 32><<<rc.totals[0], kT, 0, st>>>(rc.scans, f, n); break;
+        case 1: ragged_gather_kernel<8, 32><<<rc.totals[0], kT, 0, st>>>(rc.scans, f, n); break;
+        case 2: ragged_gather_kernel<32, 32><<<rc.totals[0], kT, 0, st>>>(rc.scans, f, n); break;
+        case 3: ragged_gather_kernel<8, 64><<<rc.totals[0], kT, 0, st>>>(rc.scans, f, n); break;
+        default: return cudaErrorInvalidValue;
+    }
+    ragged_onorm_kernel<<<rc.totals[1], kT, 0, st>>>(rc.scans, f + (n + 1), n);
+    if (rc.probe_ppt == 2)
+        ragged_ppart_kernel<2><<<rc.totals[2], kT, 0, st>>>(rc.scans, f + 2 * (n + 1), n);
+    else
+        ragged_ppart_kernel<1><<<rc.totals[2], kT, 0, st>>>(rc.scans, f + 2 * (n + 1), n);
+    ragged_preduce_kernel<<<rc.totals[3], kT, 0, st>>>(rc.scans, f + 3 * (n + 1), n);
+    ragged_pnorm_kernel<<<rc.totals[4], kT, 0, st>>>(rc.scans, f + 4 * (n + 1), rc.n_slice, n);
     return cudaGetLastError();
 }
 

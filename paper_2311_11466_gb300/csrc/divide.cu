@@ -32,30 +32,37 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "debug.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
+
+PTYCHO_DEBUG_UNIT(divide)
 
 namespace ptycho {
 namespace {
 
 // A x B radix split, cluster size C, threads T, row stride residue RSM (mod
-// 16), and the CTAs per SM the register budget is sized for (MINB).
-template <int N> struct Cfg;
-template <> struct Cfg<8>   { static constexpr int A = 4,  B = 2,  C = 1, T = 32,  RSM = 9, MINB = 4; };
-template <> struct Cfg<16>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64,  RSM = 9, MINB = 4; };
-template <> struct Cfg<32>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
-template <> struct Cfg<64>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256, RSM = 9, MINB = 4; };
-template <> struct Cfg<128> { static constexpr int A = 16, B = 8,  C = 8, T = 128, RSM = 9, MINB = 8; };
-template <> struct Cfg<256> { static constexpr int A = 16, B = 16, C = 16, T = 256, RSM = 1, MINB = 4; };
+// 16), and the CTAs per SM the register budget is sized for (MINB).  V selects
+// a launch variant with the same radix split (the same arithmetic): at 128^2
+// the autotuner times clusters of 8 CTAs of 128 threads (V = 0) against 16 of
+// 64 (V = 1).
+template <int N, int V = 0> struct Cfg;
+template <> struct Cfg<8, 0>   { static constexpr int A = 4,  B = 2,  C = 1, T = 32,  RSM = 9, MINB = 4; };
+template <> struct Cfg<16, 0>  { static constexpr int A = 4,  B = 4,  C = 1, T = 64,  RSM = 9, MINB = 4; };
+template <> struct Cfg<32, 0>  { static constexpr int A = 8,  B = 4,  C = 1, T = 128, RSM = 9, MINB = 4; };
+template <> struct Cfg<64, 0>  { static constexpr int A = 8,  B = 8,  C = 2, T = 256, RSM = 9, MINB = 4; };
+template <> struct Cfg<128, 0> { static constexpr int A = 16, B = 8,  C = 8, T = 128, RSM = 9, MINB = 8; };
+template <> struct Cfg<128, 1> { static constexpr int A = 16, B = 8,  C = 16, T = 64, RSM = 9, MINB = 16; };
+template <> struct Cfg<256, 0> { static constexpr int A = 16, B = 16, C = 16, T = 256, RSM = 1, MINB = 4; };
 
-template <int N>
+template <int N, int V = 0>
 struct Geo {
-    static constexpr int A = Cfg<N>::A, B = Cfg<N>::B, C = Cfg<N>::C, T = Cfg<N>::T;
+    static constexpr int A = Cfg<N, V>::A, B = Cfg<N, V>::B, C = Cfg<N, V>::C, T = Cfg<N, V>::T;
     static constexpr int R = N / C;       // rows per CTA
     static constexpr int KC = A / C;      // pass-2 indices k per CTA
     static constexpr int RS0 = A * (B + 1);
-    static constexpr int RS = RS0 + ((Cfg<N>::RSM - RS0 % 16) + 16) % 16;  // row stride
+    static constexpr int RS = RS0 + ((Cfg<N, V>::RSM - RS0 % 16) + 16) % 16;  // row stride
     static constexpr int TP2 = (R * A + T - 1) / T;  // pass-2 tasks per thread
     static constexpr size_t SMEM = (size_t)R * RS * sizeof(float2) + 2 * N * sizeof(float2) +
                                    32 * sizeof(double);
@@ -65,13 +72,13 @@ struct Geo {
 
 // True when passes 1 and 2 of a row DFT run on the same 16 lanes (A == B == 16
 // and one task per thread), so the hand-over between them is warp-local.
-template <int N>
-constexpr bool kRowPerHalfWarp = Geo<N>::A == 16 && Geo<N>::B == 16 && Geo<N>::R * 16 == Geo<N>::T;
+template <int N, int V>
+constexpr bool kRowPerHalfWarp = Geo<N, V>::A == 16 && Geo<N, V>::B == 16 && Geo<N, V>::R * 16 == Geo<N, V>::T;
 
 // Scratch lines are dropped from L2 once read when a row of the scratch is a
 // whole number of 128-byte lines and the lanes sharing a line sit in one warp.
-template <int N>
-constexpr bool kDiscard = (N % 16 == 0) && (Geo<N>::T % 32 == 0) && (32 % Geo<N>::B == 0);
+template <int N, int V>
+constexpr bool kDiscard = (N % 16 == 0) && (Geo<N, V>::T % 32 == 0) && (32 % Geo<N, V>::B == 0);
 
 // One bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
 // multiple of 16); it does not wait and brings nothing into the SM.
@@ -89,11 +96,12 @@ __device__ __forceinline__ void discard_l2(const void* p) {
 // sequential projections (update O and P from one exit wave).
 enum : int { kModeDivide = 0, kModeErrOnly = 1, kModeSP = 2 };
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const DivideArgs args) {
+// The work of one CTA of the cluster that handles exit wave j.
+template <int N, int MODE, int V>
+__device__ __forceinline__ void divide_body(const DivideArgs& args, const int j) {
     constexpr bool ERR_ONLY = MODE == kModeErrOnly;
     constexpr bool SP = MODE == kModeSP;
-    using G = Geo<N>;
+    using G = Geo<N, V>;
     constexpr int A = G::A, B = G::B, C = G::C, T = G::T, R = G::R, RS = G::RS;
     constexpr int TP2 = G::TP2;
     constexpr size_t NN = (size_t)N * N;
@@ -106,9 +114,6 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
     const int tid = threadIdx.x;
-    // one cluster per exit wave; a sequential-projections step works on one
-    // given position
-    const int j = SP ? args.sp_pos : (int)(blockIdx.x / C);
 
     for (int i = tid; i < N; i += T) {
         const float2 w = args.tw[i];
@@ -135,7 +140,15 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         prefetch_l2(args.sqrtIp + off, (unsigned)(R * N * sizeof(float)));
     }
     __syncthreads();  // twiddles loaded
-    const int2 s = args.pos[j];
+    int2 s = args.pos[j];
+#if PT_DBG_ENABLED
+    // checked build: a window outside the object is recorded and clamped to the
+    // corner (every CTA of the cluster still reaches its barriers)
+    if (s.x < 0 || s.y < 0 || s.x > args.Mr - N || s.y > args.Mc - N) {
+        if (tid == 0) PT_DBG_FLAG(kDbgWindow);
+        s = make_int2(0, 0);
+    }
+#endif
     const float2* Ow = args.O + (size_t)s.x * args.Mc + s.y;
 
     // Sequential projections, phase 0: max |P|^2 over the probe and max |O_j|^2
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
         for (int e = 0; e < A; ++e) v[e] = __ldcg(src + B * e);
         dft_reg<A, false>(v);
-        if constexpr (kDiscard<N>) {
+        if constexpr (kDiscard<N, V>) {
             // the B lanes of row rho (one warp) have read its N / 16 lines of S
             __syncwarp();
             const float2* line0 = S + (size_t)(c * R + rho) * N;
@@ -268,12 +281,18 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
     }
     // With A == B and one task per thread, the 16 lanes that wrote a row in
     // pass 1 are the ones that read it in pass 2: a warp barrier suffices.
-    if constexpr (kRowPerHalfWarp<N>) __syncwarp(); else __syncthreads();
+    if constexpr (kRowPerHalfWarp<N, V>) __syncwarp(); else __syncthreads();
 
     // Phase 4: column DFT pass 2, Fourier-modulus projection with the c
     // relaxation and the 1/N^2 of the inverse, inverse pass 2 and conjugate
     // twiddle (lanes over k).
-    float err = 0.f;
+    // Fourier-error partial of each column frequency v' = c R + row (N elements:
+    // A tasks of B): each task sums its B terms in order, the A lanes of the
+    // row add theirs by a fixed butterfly, and lane k = 0 stores the row's
+    // partial at e_part[j N + v'].  The grouping depends on neither the
+    // cluster shape nor the thread count, so every launch variant gives the
+    // same partials (R * A is a multiple of T: every lane takes every round).
+    static_assert((R * A) % T == 0 && T % A == 0 && A <= 32, "error-partial lanes");
     const float* sq = args.sqrtIp + pat + (size_t)c * R * N;
     const float inv_n2 = 1.0f / (float)(N * N);
     const float cr = args.c, oc = 1.0f - args.c;
@@ -285,6 +304,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
         for (int t = 0; t < B; ++t) u[t] = p[t];
         dft_reg<B, false>(u);
+        float err = 0.f;
         float sv[B];
         const float* sp = sq + (size_t)(row * A + k) * B;
         if constexpr (B % 4 == 0) {
@@ -299,6 +319,9 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
         }
 #pragma unroll
         for (int q = 0; q < B; ++q) {
+#if PT_DBG_ENABLED
+            if (!(sv[q] >= 0.f) || !isfinite(sv[q])) PT_DBG_FLAG(kDbgSqrtI);
+#endif
             // |Psi| and Psi/|Psi| from one reciprocal square root
             const float m2 = cabs2(u[q]);
             const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
@@ -311,6 +334,9 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
                                 : make_float2(cr * sv[q] * inv_n2, 0.f);
             }
         }
+#pragma unroll
+        for (int o = A / 2; o > 0; o >>= 1) err += __shfl_xor_sync(0xffffffffu, err, o, A);
+        if (k == 0) args.e_part[(size_t)j * N + c * R + row] = (double)err;
         if constexpr (!ERR_ONLY) {
             dft_reg<B, true>(u);
 #pragma unroll
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
                 for (int t = 0; t < B; ++t) u[t] = __ldcg(src + t);
             }
-            if constexpr (kDiscard<N>) {
+            if constexpr (kDiscard<N, V>) {
                 // the lanes reading one 128-byte line are in this warp
                 __syncwarp();
                 if ((k * B) % 16 == 0) discard_l2(src);
@@ -364,7 +390,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
 #pragma unroll
             for (int t = 0; t < B; ++t) p[t] = cconjmul(twB[t * A + k], u[t]);
         }
-        if constexpr (kRowPerHalfWarp<N>) __syncwarp(); else __syncthreads();
+        if constexpr (kRowPerHalfWarp<N, V>) __syncwarp(); else __syncthreads();
 
         // Phase 7: row inverse pass 1, store y_k (lanes over t).
 #pragma unroll 1
@@ -387,35 +413,32 @@ __global__ void __launch_bounds__(Geo<N>::T, Cfg<N>::MINB) divide_kernel(const D
                     const float2 d = csub(v[e], cmul_rn(pv, ov));
                     *op = cadd(ov, cscale(cconjmul(pv, d), inv_maxP));
                     args.P_mut[r * N + n] = cadd(pv, cscale(cconjmul(ov, d), inv_maxO));
+#if PT_DBG_ENABLED
+                    if (PT_DBG_NONFINITE2(*op) || PT_DBG_NONFINITE2(args.P_mut[r * N + n]))
+                        PT_DBG_FLAG(kDbgNonFinite);
+#endif
                 }
             } else {
                 float2* yo = args.y + pat + (size_t)r * N + t;
 #pragma unroll
-                for (int e = 0; e < A; ++e) __stcs(yo + B * e, v[e]);
+                for (int e = 0; e < A; ++e) {
+#if PT_DBG_ENABLED
+                    if (PT_DBG_NONFINITE2(v[e])) PT_DBG_FLAG(kDbgNonFinite);
+#endif
+                    __stcs(yo + B * e, v[e]);
+                }
             }
         }
     }
 
-    // CTA partial in FP32 (FP64 is slow on this part); the sum over all CTAs
-    // is taken in FP64 by the concur step
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) err += __shfl_down_sync(0xffffffffu, err, o);
-    if ((tid & 31) == 0) redf[tid >> 5] = err;
-    __syncthreads();
-    if (tid == 0) {
-        float tot = 0.f;
-#pragma unroll
-        for (int w = 0; w < T / 32; ++w) tot += redf[w];
-        args.e_part[(size_t)j * C + c] = (double)tot;
-    }
 }
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(256) sqrt_permute_kernel(const float* __restrict__ I,
                                                            float* __restrict__ sqrtIp,
                                                            double* __restrict__ psum,
                                                            int* __restrict__ bad) {
-    using G = Geo<N>;
+    using G = Geo<N, V>;
     constexpr int A = G::A, B = G::B, R = G::R, KC = G::KC;
     __shared__ double red[8];
     const int j = blockIdx.y;
@@ -434,39 +457,102 @@ __global__ void __launch_bounds__(256) sqrt_permute_kernel(const float* __restri
         const float val = I[(size_t)j * N * N + (size_t)u * N + v];
         if (!(val >= 0.0f) || !isfinite(val)) atomicOr(bad, 1);
         sqrtIp[(size_t)j * N * N + pidx] = sqrtf(fmaxf(val, 0.0f));
-        v64 = (double)val;
+        // the sums run over blocks of the natural order, so sum I (and every
+        // Fourier error) does not depend on the layout of sqrt(I)
+        v64 = (double)I[(size_t)j * N * N + pidx];
     }
     const double tot = block_sum_double<256>(v64, red);
     if (threadIdx.x == 0) psum[(size_t)j * gridDim.x + blockIdx.x] = tot;
 }
 
-template <int N>
+// One cluster per exit wave; a sequential-projections step works on one given
+// position.
+template <int N, int MODE, int V>
+__global__ void __launch_bounds__(Geo<N, V>::T, Cfg<N, V>::MINB) divide_kernel(const DivideArgs args) {
+    divide_body<N, MODE, V>(args, MODE == kModeSP ? args.sp_pos : (int)(blockIdx.x / Geo<N, V>::C));
+}
+
+// The divide step of several scans of side N in one launch (batching): the
+// clusters are numbered over all their exit waves, scan s owning waves
+// first[s] .. first[s + 1] - 1; each cluster runs the same work with its
+// scan's arguments, so every scan's result is that of its own launch.
+template <int N, int V>
+__global__ void __launch_bounds__(Geo<N, V>::T, Cfg<N, V>::MINB)
+    divide_ragged_kernel(const DivideArgs* __restrict__ table, const int* __restrict__ first,
+                         int n_scans) {
+    const int g = (int)(blockIdx.x / Geo<N, V>::C);
+    int s = 0;
+    while (s + 1 < n_scans && first[s + 1] <= g) ++s;
+    divide_body<N, kModeDivide, V>(table[s], g - first[s]);
+}
+
+// Index in the permuted sqrt(I) layout of variant V of row frequency u and
+// column frequency v (the inverse of the map in sqrt_permute_kernel).
+template <int N, int V>
+__device__ __forceinline__ int permuted_index(int u, int v) {
+    using G = Geo<N, V>;
+    constexpr int A = G::A, B = G::B, R = G::R, KC = G::KC;
+    const int k1p = u % A, k2p = u / A;
+    const int rho = ((v % A) % KC) * B + v / A;
+    const int cta = (v % A) / KC;
+    return ((cta * R + rho) * A + k1p) * B + k2p;
+}
+
+// sqrt(I) from the layout of variant VF (src) to that of variant VT (dst).
+template <int N, int VF, int VT>
+__global__ void __launch_bounds__(256) relayout_kernel(const float* __restrict__ src,
+                                                       float* __restrict__ dst) {
+    using G = Geo<N, VT>;
+    constexpr int A = G::A, B = G::B, R = G::R, KC = G::KC;
+    const int j = blockIdx.y;
+    const int pidx = blockIdx.x * 256 + threadIdx.x;
+    if (pidx >= N * N) return;
+    const int k2p = pidx % B;
+    int tmp = pidx / B;
+    const int k1p = tmp % A;
+    tmp /= A;
+    const int rho = tmp % R;
+    const int cta = tmp / R;
+    const int u = k1p + A * k2p;
+    const int v = (cta * KC + rho / B) + A * (rho % B);
+    dst[(size_t)j * N * N + pidx] = src[(size_t)j * N * N + permuted_index<N, VF>(u, v)];
+}
+
+template <int N, int V = 0>
 cudaError_t prepare_t() {
-    cudaError_t e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide>,
+    cudaError_t e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide, V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<N>::SMEM);
+                                         (int)Geo<N, V>::SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(divide_kernel<N, kModeSP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Geo<N>::SMEM);
+    e = cudaFuncSetAttribute(divide_ragged_kernel<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<N, V>::SMEM);
     if (e != cudaSuccess) return e;
-    if constexpr (Geo<N>::C > 8) {  // clusters above the portable size of 8
-        e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(divide_kernel<N, kModeSP>,
+    if constexpr (Geo<N, V>::C > 8) {
+        e = cudaFuncSetAttribute(divide_ragged_kernel<N, V>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<N>::SMEM);
+    e = cudaFuncSetAttribute(divide_kernel<N, kModeSP, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<N, V>::SMEM);
+    if (e != cudaSuccess) return e;
+    if constexpr (Geo<N, V>::C > 8) {  // clusters above the portable size of 8
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeDivide, V>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly, V>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(divide_kernel<N, kModeSP, V>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaFuncSetAttribute(divide_kernel<N, kModeErrOnly, V>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<N, V>::SMEM);
 }
 
-template <int N>
+template <int N, int V = 0>
 cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
-    using G = Geo<N>;
+    using G = Geo<N, V>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)a.J * G::C);
     cfg.blockDim = dim3(G::T);
@@ -486,26 +572,74 @@ cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     cfg.numAttrs = 2;
     if (a.sp) {
         cfg.gridDim = dim3((unsigned)G::C);  // one cluster: one position
-        return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeSP>, a);
+        return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeSP, V>, a);
     }
-    if (a.err_only) return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeErrOnly>, a);
-    return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeDivide>, a);
+    if (a.err_only) return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeErrOnly, V>, a);
+    return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeDivide, V>, a);
 }
 
-template <int N>
+template <int N, int V = 0>
+cudaError_t launch_ragged_t(const DivideArgs* table, const int* first, int n, int total_waves,
+                            cudaStream_t st) {
+    using G = Geo<N, V>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)total_waves * G::C);
+    cfg.blockDim = dim3(G::T);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, divide_ragged_kernel<N, V>, table, first, n);
+}
+
+template <int N, int V = 0>
 cudaError_t sqrt_t(const float* I, float* sqrtIp, double* psum, int* bad, int J, cudaStream_t st) {
     dim3 grid((N * N + 255) / 256, J);
-    sqrt_permute_kernel<N><<<grid, 256, 0, st>>>(I, sqrtIp, psum, bad);
+    sqrt_permute_kernel<N, V><<<grid, 256, 0, st>>>(I, sqrtIp, psum, bad);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_divide_ragged(int N, int variant, const DivideArgs* table, const int* first,
+                                 int n, int total_waves, cudaStream_t st) {
+    switch (N) {
+        case 8: return launch_ragged_t<8>(table, first, n, total_waves, st);
+        case 16: return launch_ragged_t<16>(table, first, n, total_waves, st);
+        case 32: return launch_ragged_t<32>(table, first, n, total_waves, st);
+        case 64: return launch_ragged_t<64>(table, first, n, total_waves, st);
+        case 128:
+            return variant == 1 ? launch_ragged_t<128, 1>(table, first, n, total_waves, st)
+                                : launch_ragged_t<128, 0>(table, first, n, total_waves, st);
+        case 256: return launch_ragged_t<256>(table, first, n, total_waves, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_relayout_sqrt(int N, int from, int to, const float* src, float* dst, int J,
+                                 cudaStream_t st) {
+    if (N != 128 || from == to || from < 0 || from > 1 || to < 0 || to > 1) return cudaErrorInvalidValue;
+    dim3 grid((N * N + 255) / 256, J);
+    if (from == 0)
+        relayout_kernel<128, 0, 1><<<grid, 256, 0, st>>>(src, dst);
+    else
+        relayout_kernel<128, 1, 0><<<grid, 256, 0, st>>>(src, dst);
+    return cudaGetLastError();
+}
+
 bool divide_supported(int N) {
     return N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || N == 256;
 }
 
-int divide_cluster_size(int N) {
+int divide_cluster_size(int N, int variant) {
+    if (N == 128 && variant == 1) return Geo<128, 1>::C;
     switch (N) {
         case 8: return Geo<8>::C;
         case 16: return Geo<16>::C;
@@ -545,7 +679,10 @@ cudaError_t divide_prepare(int N) {
         case 16: return prepare_t<16>();
         case 32: return prepare_t<32>();
         case 64: return prepare_t<64>();
-        case 128: return prepare_t<128>();
+        case 128: {
+            cudaError_t e = prepare_t<128, 0>();
+            return e != cudaSuccess ? e : prepare_t<128, 1>();
+        }
         case 256: return prepare_t<256>();
     }
     return cudaErrorInvalidValue;
@@ -558,14 +695,15 @@ cudaError_t launch_divide(int N, const DivideArgs& a, cudaStream_t st) {
         case 16: return launch_t<16>(a, st);
         case 32: return launch_t<32>(a, st);
         case 64: return launch_t<64>(a, st);
-        case 128: return launch_t<128>(a, st);
+        case 128: return a.variant == 1 ? launch_t<128, 1>(a, st) : launch_t<128, 0>(a, st);
         case 256: return launch_t<256>(a, st);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sqrt_permute(int N, const float* I, float* sqrtIp, double* psum, int* bad,
-                                int J, cudaStream_t st) {
+cudaError_t launch_sqrt_permute(int N, int variant, const float* I, float* sqrtIp, double* psum,
+                                int* bad, int J, cudaStream_t st) {
+    if (N == 128 && variant == 1) return sqrt_t<128, 1>(I, sqrtIp, psum, bad, J, st);
     switch (N) {
         case 8: return sqrt_t<8>(I, sqrtIp, psum, bad, J, st);
         case 16: return sqrt_t<16>(I, sqrtIp, psum, bad, J, st);

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/ptycho.h"
+#include "debug.cuh"
 #include "internal.h"
 #include "nvtx.h"
 
@@ -25,6 +26,10 @@ namespace {
 
 constexpr int kRing = 65536;  // error-history entries kept on the device
 constexpr int kProfMax = 4096;  // iterations the timing hook can record
+// Design of the FP32 divide step that PTYCHO_DIVIDE_AUTO picks at N = 256
+// (the faster of the two on the 1024 x 256^2 workload); other N have only the
+// cluster design.
+constexpr int kAutoDivide256 = PTYCHO_DIVIDE_CLUSTER;
 
 thread_local std::string g_create_error;
 
@@ -38,11 +43,16 @@ struct ptycho_ctx {
 
     bool loaded = false;
     int J = 0, N = 0, Mr = 0, Mc = 0, C = 0;
+    int n_part = 0;  // Fourier-error partials the divide design writes per iteration
     double sumI = 0.0;
 
     float2 *x = nullptr, *y = nullptr, *P = nullptr, *O = nullptr, *tw = nullptr;
     float* sqrtIp = nullptr;
-    float2* scratch = nullptr;  // divide-kernel transpose scratch, one slot per exit wave
+    int divide = PTYCHO_DIVIDE_CLUSTER;  // resolved divide design of the current scan
+    int variant = 0;                     // cluster design: launch variant (128^2 tuned)
+    float2* scratch = nullptr;  // cluster design: transpose scratch, one slot per exit wave;
+                                // two-pass design: a ring of slots (Fourier error only, SP)
+    unsigned* ctl = nullptr;    // two-pass design: ticket and completion counts
     // tensor-core path: sqrt(I) in the patterns' layout, two ping-pong operand buffers (hi,
     // lo) and the constant DFT operands (fwd hi, fwd lo, inv hi, inv lo)
     float* sqrtI = nullptr;
@@ -59,6 +69,10 @@ struct ptycho_ctx {
     bool have_x = true;
     float pa = 1.f, pb = 1.f;
     int64_t iters = 0;
+    int32_t probe_start = 0;  // iterations k < probe_start hold the probe fixed
+    bool tuned = false;         // launch shapes of the concur kernels chosen
+    bool tuning = true;         // choose them at the first iteration (ptycho_set_tuning)
+    std::vector<int32_t> pos_h; // host copy of the positions (tile lists)
 
     // measurement: three events per recorded iteration
     bool prof = false;
@@ -113,6 +127,7 @@ void free_scan(ptycho_ctx* ctx) {
     ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;
     ctx->sqrtIp = nullptr;
     ctx->scratch = nullptr;
+    ctx->ctl = nullptr;
     ctx->sqrtI = nullptr;
     for (int i = 0; i < 4; ++i) ctx->planes[i] = ctx->Bc[i] = nullptr;
     ctx->pos = nullptr;
@@ -143,17 +158,69 @@ struct DeviceGuard {
     }
 };
 
-// After a synchronisation: a bounded device wait of the tensor-core kernels
-// that expired leaves a flag; report it once.
+// After a synchronisation: a bounded device wait that expired (bit 0: the
+// tensor-core DFT kernel; bit 1: the two-pass divide kernel) leaves a flag;
+// report it once.
 int check_device_flags(ptycho_ctx* ctx) {
-    if (ctx->opts.precision != PTYCHO_PREC_BF16X3 || !ctx->dflag) return PTYCHO_OK;
+    if (!ctx->dflag || (ctx->opts.precision != PTYCHO_PREC_BF16X3 && ctx->divide != PTYCHO_DIVIDE_TWOPASS))
+        return PTYCHO_OK;
     int f = 0;
     PT_CUDA(ctx, cudaMemcpy(&f, ctx->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) {
         PT_CUDA(ctx, cudaMemset(ctx->dflag + 1, 0, sizeof(int)));
-        return fail(ctx, PTYCHO_ETIMEOUT, "a bounded wait in the tensor-core DFT kernel expired");
+        return fail(ctx, PTYCHO_ETIMEOUT, (f & 1) ? "a bounded wait in the tensor-core DFT kernel expired"
+                                                  : "a bounded wait in the two-pass divide kernel expired");
     }
     return PTYCHO_OK;
+}
+
+// Arguments of the divide kernels common to every call of a context.
+DivideArgs divide_args(ptycho_ctx* ctx) {
+    DivideArgs da{};
+    da.x = ctx->x;
+    da.y = ctx->y;
+    da.sqrtIp = ctx->sqrtIp;
+    da.P = ctx->P;
+    da.O = ctx->O;
+    da.pos = ctx->pos;
+    da.tw = ctx->tw;
+    da.e_part = ctx->e_part;
+    da.J = ctx->J;
+    da.Mr = ctx->Mr;
+    da.Mc = ctx->Mc;
+    da.scratch = ctx->scratch;
+    da.ctl = ctx->ctl;
+    da.lag = divide2p_lag();
+    da.ring = ctx->J < divide2p_ring() ? ctx->J : divide2p_ring();
+    da.err_flag = ctx->dflag + 1;
+    da.variant = ctx->variant;
+    return da;
+}
+
+ConcurScan concur_scan(ptycho_ctx* ctx, int n_part) {
+    ConcurScan cs{};
+    cs.y = ctx->y;
+    cs.P = ctx->P;
+    cs.O = ctx->O;
+    cs.pos = ctx->pos;
+    cs.cb = ctx->cb;
+    cs.J = ctx->J;
+    cs.N = ctx->N;
+    cs.Mr = ctx->Mr;
+    cs.Mc = ctx->Mc;
+    cs.alpha = (double)ctx->opts.alpha;
+    cs.e_part = ctx->e_part;
+    cs.n_part = n_part;
+    cs.inv_sumI = ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0;
+    cs.e_ring = ctx->e_ring;
+    cs.d_iter = ctx->d_iter;
+    cs.ring_cap = kRing;
+    return cs;
+}
+
+cudaError_t launch_divide_ctx(ptycho_ctx* ctx, const DivideArgs& da) {
+    return ctx->divide == PTYCHO_DIVIDE_TWOPASS ? launch_divide2p(da, ctx->stream)
+                                                : launch_divide(ctx->N, da, ctx->stream);
 }
 
 int materialise(ptycho_ctx* ctx) {
@@ -171,6 +238,37 @@ cudaStream_t ctx_stream(const ptycho_ctx* ctx) { return ctx->stream; }
 int ctx_device(const ptycho_ctx* ctx) { return ctx->opts.device; }
 bool ctx_loaded(const ptycho_ctx* ctx) { return ctx->loaded; }
 void ctx_add_iterations(ptycho_ctx* ctx, int64_t n) { ctx->iters += n; }
+bool ctx_ragged_iteration(ptycho_ctx* ctx, float a, float b, float c, DivideArgs* da,
+                          ConcurScan* cs, int* N, int* variant) {
+    if (!ctx->loaded || ctx->have_x || ctx->opts.precision != PTYCHO_PREC_FP32 ||
+        ctx->divide != PTYCHO_DIVIDE_CLUSTER || ctx->opts.concur != PTYCHO_CONCUR_DETERMINISTIC ||
+        ctx->iters < ctx->probe_start || !ctx->tuned)
+        return false;
+    *da = divide_args(ctx);
+    da->load_x = 0;
+    da->pa = ctx->pa;
+    da->pb = ctx->pb;
+    da->c = c;
+    da->write_x = a != 1.0f ? 1 : 0;
+    da->err_only = 0;
+    *cs = concur_scan(ctx, ctx->n_part);
+    *N = ctx->N;
+    *variant = ctx->variant;
+    (void)b;
+    return true;
+}
+
+void ctx_ragged_done(ptycho_ctx* ctx, float a, float b, int64_t n) {
+    if (n <= 0) return;
+    ctx->have_x = false;
+    ctx->pa = a;
+    ctx->pb = b;
+    ctx->iters += n;
+}
+
+int64_t ctx_probe_hold(const ptycho_ctx* ctx) {
+    return ctx->iters < ctx->probe_start ? ctx->probe_start - ctx->iters : 0;
+}
 }  // namespace ptycho
 
 extern "C" {
@@ -182,6 +280,7 @@ void ptycho_default_opts(ptycho_opts* o) {
     o->concur = PTYCHO_CONCUR_DETERMINISTIC;
     o->alpha = 1e-6f;
     o->stream = nullptr;
+    o->divide = PTYCHO_DIVIDE_AUTO;
 }
 
 int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts) {
@@ -204,6 +303,11 @@ int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts) {
     }
     if (!(o.alpha >= 0.0f) || !std::isfinite(o.alpha)) {
         g_create_error = "alpha must be finite and >= 0";
+        return PTYCHO_EINVAL;
+    }
+    if (o.divide != PTYCHO_DIVIDE_AUTO && o.divide != PTYCHO_DIVIDE_CLUSTER &&
+        o.divide != PTYCHO_DIVIDE_TWOPASS) {
+        g_create_error = "unknown divide design";
         return PTYCHO_EINVAL;
     }
     int ndev = 0;
@@ -250,34 +354,55 @@ const char* ptycho_last_error(const ptycho_ctx* ctx) {
 }
 
 size_t ptycho_scan_bytes(int32_t J, int32_t N, int32_t M_rows, int32_t M_cols, int precision) {
+    return ptycho::scan_bytes(J, N, M_rows, M_cols, precision, PTYCHO_DIVIDE_AUTO);
+}
+
+int ptycho_divide_design(const ptycho_ctx* ctx) { return ctx && ctx->loaded ? ctx->divide : 0; }
+
+}  // extern "C"
+
+int ptycho::resolve_divide(int precision, int divide, int N) {
+    if (precision == PTYCHO_PREC_BF16X3 || !divide2p_supported(N)) return PTYCHO_DIVIDE_CLUSTER;
+    if (divide == PTYCHO_DIVIDE_TWOPASS || divide == PTYCHO_DIVIDE_CLUSTER) return divide;
+    return kAutoDivide256;
+}
+
+size_t ptycho::scan_bytes(int J, int N, int M_rows, int M_cols, int precision, int divide) {
     if (J <= 0 || N <= 0 || M_rows <= 0 || M_cols <= 0) return 0;
+    const bool two = resolve_divide(precision, divide, N) == PTYCHO_DIVIDE_TWOPASS;
     const size_t NN = (size_t)N * N, M = (size_t)M_rows * M_cols;
-    const int C = divide_cluster_size(N) > 0 ? divide_cluster_size(N) : 1;
     const size_t chunks = (size_t)probe_chunks(J, N);
-    const int tiles = ((M_rows + kObjTileR - 1) / kObjTileR) * ((M_cols + kObjTile - 1) / kObjTile);
-    const int tr_per = (N + kObjTileR - 1) / kObjTileR + 1;
     size_t b = 0;
     b += 2 * (size_t)J * NN * sizeof(float2);        // x, y
     b += (size_t)J * NN * sizeof(float);             // sqrt(I)
     b += 2 * NN * sizeof(float2) + M * sizeof(float2);  // P, tw, O
     b += (size_t)J * sizeof(int2);
-    b += (size_t)J * C * sizeof(double) + (size_t)kRing * sizeof(double) + 64;
-    b += M * (sizeof(float2) + sizeof(float)) + 16;
+    const size_t parts_fp32 = (size_t)J * (N > 16 ? N : 16);  // either divide design
+    b += parts_fp32 * sizeof(double) + (size_t)kRing * sizeof(double) + 64;
+    b += M * (sizeof(float2) + sizeof(double)) + 16;
     b += chunks * NN * (sizeof(float2) + sizeof(float));
     b += NN * (sizeof(double2) + sizeof(double));
     b += (size_t)probe_reduce_blocks(N, (int)chunks) * sizeof(double);  // error slice totals
-    b += (size_t)(tiles + 1) * sizeof(int) + (size_t)J * tr_per * (N / kObjTile + 1) * sizeof(int4);
+    b += tile_csr_ptr_bound(N, M_rows, M_cols) * sizeof(int) + tile_csr_entries_bound(J, N) * sizeof(int4);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
-    b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
+    if (two) {
+        const int ring = J < divide2p_ring() ? J : divide2p_ring();
+        b += (size_t)ring * NN * sizeof(float2);                    // scratch ring
+        b += divide2p_ctl_words(J) * sizeof(unsigned);              // ticket and counts
+    } else {
+        b += (size_t)(J > 2 ? J : 2) * NN * sizeof(float2);  // transpose scratch
+    }
     if (precision == PTYCHO_PREC_BF16X3) {
         b += (size_t)J * NN * sizeof(float);           // sqrt(I), patterns' layout
         b += 4 * (size_t)J * NN * 2 * sizeof(uint16_t);  // two operand buffers, hi + lo
         b += 4 * 4 * NN * sizeof(uint16_t);            // constant DFT operands
         const size_t parts = (size_t)bf16x3_error_parts(N, J);  // a second, larger error buffer
-        if (parts > (size_t)J * C) b += parts * sizeof(double);
+        if (parts > parts_fp32) b += parts * sizeof(double);
     }
     return b;
 }
+
+extern "C" {
 
 int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_rc,
                      const float* intensity, int32_t M_rows, int32_t M_cols, const float* obj0,
@@ -311,32 +436,23 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     free_scan(ctx);
 
     // Object tiles: CSR lists of the positions whose window overlaps each tile,
-    // in ascending position order (integer work, done here).
-    const int tiles_r = (M_rows + kObjTileR - 1) / kObjTileR;
-    const int tiles_c = (M_cols + kObjTile - 1) / kObjTile;
-    std::vector<int> tile_cnt((size_t)tiles_r * tiles_c + 1, 0);
-    for (int j = 0; j < J; ++j) {
-        const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
-        for (int ti = r / kObjTileR; ti <= (r + N - 1) / kObjTileR; ++ti)
-            for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
-                tile_cnt[(size_t)ti * tiles_c + tj + 1]++;
-    }
-    for (size_t t = 1; t < tile_cnt.size(); ++t) tile_cnt[t] += tile_cnt[t - 1];
-    std::vector<int4> tile_list((size_t)tile_cnt.back());
-    {
-        std::vector<int> fill(tile_cnt.begin(), tile_cnt.end() - 1);
-        for (int j = 0; j < J; ++j) {
-            const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
-            for (int ti = r / kObjTileR; ti <= (r + N - 1) / kObjTileR; ++ti)
-                for (int tj = c / kObjTile; tj <= (c + N - 1) / kObjTile; ++tj)
-                    tile_list[(size_t)fill[(size_t)ti * tiles_c + tj]++] = make_int4(j, r, c, 0);
-        }
-    }
+    // in ascending position order (integer work, done here), for the tile
+    // shape the tuner chose for this kind of scan (or the default).
+    const TuneChoice tuned = tune_lookup(ctx->opts.device, N, J);
+    std::vector<int> tile_cnt;
+    std::vector<int4> tile_list;
+    build_tile_csr(pos_rc, J, N, M_rows, M_cols, kGatherShape[tuned.gather_shape], tile_cnt, tile_list);
+    const TileShape shape = kGatherShape[tuned.gather_shape];
+    const int tiles_r = (M_rows + shape.rows - 1) / shape.rows;
+    const int tiles_c = (M_cols + shape.cols - 1) / shape.cols;
 
     const int C = divide_cluster_size(N);
     const int chunks = probe_chunks(J, N);
+    const int design = resolve_divide(ctx->opts.precision, ctx->opts.divide, N);
+    const bool two = design == PTYCHO_DIVIDE_TWOPASS;
     {
         cudaError_t pe = divide_prepare(N);
+        if (pe == cudaSuccess && two) pe = divide2p_prepare();
         if (pe != cudaSuccess) return cuda_fail(ctx, pe, "divide_prepare");
     }
     const int sq_blocks = (int)((NN + 255) / 256);
@@ -352,12 +468,18 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->x, (size_t)J * NN);
     PT_ALLOC(ctx->y, (size_t)J * NN);
     PT_ALLOC(ctx->sqrtIp, (size_t)J * NN);
-    PT_ALLOC(ctx->scratch, (size_t)(J > 2 ? J : 2) * NN);  // SP steps use two slots
+    if (two) {
+        PT_ALLOC(ctx->scratch, (size_t)(J < divide2p_ring() ? J : divide2p_ring()) * NN);
+        PT_ALLOC(ctx->ctl, divide2p_ctl_words(J));
+    } else {
+        PT_ALLOC(ctx->scratch, (size_t)(J > 2 ? J : 2) * NN);  // SP steps use two slots
+    }
     PT_ALLOC(ctx->P, NN);
     PT_ALLOC(ctx->tw, (size_t)N);
     PT_ALLOC(ctx->O, M);
     PT_ALLOC(ctx->pos, (size_t)J);
-    PT_ALLOC(ctx->e_part, (size_t)J * C);
+    const size_t parts_fp32 = (size_t)J * (N > 16 ? N : 16);  // either divide design
+    PT_ALLOC(ctx->e_part, parts_fp32);
     PT_ALLOC(ctx->e_ring, (size_t)kRing);
     PT_ALLOC(ctx->e_tmp, (size_t)4);
     PT_ALLOC(ctx->d_iter, (size_t)1);
@@ -371,15 +493,16 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.e_slice, (size_t)probe_reduce_blocks(N, chunks));
     PT_ALLOC(ctx->cb.denP, NN);
     PT_ALLOC(ctx->cb.maxP, (size_t)1);
-    PT_ALLOC(ctx->cb.tile_ptr, tile_cnt.size());
-    PT_ALLOC(ctx->cb.tile_win, tile_list.size() > 0 ? tile_list.size() : 1);
+    // sized for every tile shape, so the tuner can switch shapes in place
+    PT_ALLOC(ctx->cb.tile_ptr, tile_csr_ptr_bound(N, M_rows, M_cols));
+    PT_ALLOC(ctx->cb.tile_win, tile_csr_entries_bound(J, N) > 0 ? tile_csr_entries_bound(J, N) : 1);
     PT_ALLOC(psum, (size_t)J * sq_blocks);
     if (tc) {
         PT_ALLOC(ctx->sqrtI, (size_t)J * NN);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->Bc[i], 4 * NN);
         const int tiles = bf16x3_error_parts(N, J);
-        if (tiles > J * C) {
+        if ((size_t)tiles > parts_fp32) {
             double* more = nullptr;
             PT_ALLOC(more, (size_t)tiles);
             ctx->e_part = more;  // the larger buffer serves both paths
@@ -389,11 +512,17 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     ctx->cb.tiles_r = tiles_r;
     ctx->cb.tiles_c = tiles_c;
     ctx->cb.chunks = chunks;
+    ctx->cb.gather_shape = tuned.gather_shape;
+    ctx->cb.probe_ppt = tuned.probe_ppt;
+    ctx->tuned = tuned.valid;
+    ctx->pos_h.assign(pos_rc, pos_rc + 2 * (size_t)J);
     ctx->J = J;
     ctx->N = N;
     ctx->Mr = M_rows;
     ctx->Mc = M_cols;
     ctx->C = C;
+    ctx->divide = design;
+    ctx->n_part = J * divide_error_parts_per_wave(N, two);
 
     std::vector<float2> tw;
     divide_twiddles(N, tw);
@@ -421,7 +550,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
                                 cudaMemcpyHostToDevice, st));
     PT_STEP(cudaMemsetAsync(ctx->dflag, 0, 4 * sizeof(int), st));
     PT_STEP(cudaMemsetAsync(ctx->d_iter, 0, sizeof(unsigned long long), st));
-    PT_STEP(cudaMemsetAsync(ctx->cb.maxO, 0, sizeof(unsigned), st));
+    PT_STEP(cudaMemsetAsync(ctx->cb.maxO, 0, sizeof(unsigned long long), st));
     PT_STEP(cudaMemsetAsync(ctx->cb.maxP, 0, sizeof(unsigned long long), st));
     // The intensities pass through the y buffer (twice their size) on their way
     // to the permuted sqrt(I) layout.
@@ -431,7 +560,46 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
                                 cudaMemcpyHostToDevice, st));
         Idev = reinterpret_cast<const float*>(ctx->y);
     }
-    PT_STEP(launch_sqrt_permute(N, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
+    // 128^2 cluster shape: the cached choice, or timed now on this scan
+    int variant = 0;
+    if (N == 128 && !two && !tc) {
+        if (tuned.divide_tuned) {
+            variant = tuned.divide_variant;
+        } else if (ctx->tuning) {
+            float ms[2] = {0.f, 0.f};
+            for (int v = 0; v < 2; ++v) {
+                PT_STEP(launch_sqrt_permute(N, v, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
+                DivideArgs da = divide_args(ctx);
+                da.variant = v;
+                da.load_x = 0;
+                da.pa = da.pb = da.c = 1.f;
+                da.err_only = 1;   // writes only the error partials and the scratch
+                cudaEvent_t e0, e1;
+                PT_STEP(cudaEventCreate(&e0));
+                PT_STEP(cudaEventCreate(&e1));
+                e = launch_divide(N, da, st);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    if (rep == 1) e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess) e = launch_divide(N, da, st);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (e != cudaSuccess) return bail(e, "128^2 cluster-shape timing");
+                ms[v] /= 2.f;
+            }
+            variant = ms[1] < ms[0] ? 1 : 0;
+            tune_store_divide(ctx->opts.device, N, J, variant, ms);
+        }
+    }
+    ctx->variant = variant;
+    ctx->C = divide_cluster_size(N, variant);
+    if (two)
+        PT_STEP(launch_sqrt_permute2p(Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
+    else
+        PT_STEP(launch_sqrt_permute(N, variant, Idev, ctx->sqrtIp, psum, ctx->dflag, J, st));
     if (tc) {
         PT_STEP(bf16x3_prepare());
         PT_STEP(launch_sqrt_intensity(N, Idev, ctx->sqrtI, J, st));
@@ -472,41 +640,40 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
     if (n_iter < 0) return fail(ctx, PTYCHO_EINVAL, "n_iter must be >= 0");
     if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
     DeviceGuard dg(ctx->opts.device);
-    const double inv_sumI = ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0;
     for (int it = 0; it < n_iter; ++it) {
-        DivideArgs da{};
-        da.x = ctx->x;
-        da.y = ctx->y;
-        da.sqrtIp = ctx->sqrtIp;
-        da.P = ctx->P;
-        da.O = ctx->O;
-        da.pos = ctx->pos;
-        da.tw = ctx->tw;
-        da.e_part = ctx->e_part;
-        da.J = ctx->J;
-        da.Mc = ctx->Mc;
+        DivideArgs da = divide_args(ctx);
         da.load_x = ctx->have_x ? 1 : 0;
         da.pa = ctx->pa;
         da.pb = ctx->pb;
         da.c = c;
         da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;
         da.err_only = 0;
-        da.scratch = ctx->scratch;
         const bool rec = ctx->prof && ctx->prof_n < kProfMax;
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
-        int n_part = ctx->J * ctx->C;
+        int n_part = ctx->n_part;
         if (ctx->opts.precision == PTYCHO_PREC_BF16X3) {
             PT_CUDA(ctx, launch_divide_bf16x3(da, ctx->N, ctx->sqrtI, ctx->planes, ctx->Bc,
                                               ctx->dflag + 1, ctx->stream));
             n_part = bf16x3_error_parts(ctx->N, ctx->J);
         } else {
-            PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+            PT_CUDA(ctx, launch_divide_ctx(ctx, da));
         }
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 1], ctx->stream));
-        PT_CUDA(ctx, launch_concur(ctx->y, ctx->P, ctx->O, ctx->pos, ctx->cb, ctx->J, ctx->N,
-                                   ctx->Mr, ctx->Mc, ctx->opts.alpha, ctx->e_part,
-                                   n_part, inv_sumI, ctx->e_ring, ctx->d_iter, kRing,
-                                   ctx->opts.concur, ctx->stream));
+        if (!ctx->tuned && ctx->tuning && ctx->opts.concur == PTYCHO_CONCUR_DETERMINISTIC) {
+            // launch shapes of the concur kernels: the cached choice, or timed now
+            // on this iteration's divided exit waves (not while a graph is captured)
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            PT_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+            if (cs == cudaStreamCaptureStatusNone) {
+                TuneChoice tc{};
+                ConcurScan cscan = concur_scan(ctx, n_part);
+                PT_CUDA(ctx, tune_concur(ctx->opts.device, cscan, ctx->pos_h.data(), ctx->stream, &tc));
+                ctx->cb = cscan.cb;
+                ctx->tuned = true;
+            }
+        }
+        PT_CUDA(ctx, launch_concur(concur_scan(ctx, n_part), ctx->opts.concur,
+                                   ctx->iters >= ctx->probe_start, ctx->stream));
         if (rec) {
             PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 2], ctx->stream));
             ctx->prof_n++;
@@ -516,6 +683,96 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
         ctx->pb = b;
         ctx->iters++;
     }
+    return PTYCHO_OK;
+}
+
+int ptycho_debug_build(void) { return PT_DBG_ENABLED; }
+
+int ptycho_debug_flags(int device, uint32_t* flags) {
+    if (!flags) return PTYCHO_EINVAL;
+    *flags = 0u;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PTYCHO_EINVAL;
+    }
+    DeviceGuard dg(device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return PTYCHO_ECUDA;
+    unsigned a = 0, b = 0, c = 0;
+    if (debug_flags_divide(&a) != cudaSuccess || debug_flags_divide2p(&b) != cudaSuccess ||
+        debug_flags_concur(&c) != cudaSuccess)
+        return PTYCHO_ECUDA;
+    *flags = a | b | c;
+    return PTYCHO_OK;
+}
+
+int ptycho_set_tuning(ptycho_ctx* ctx, int enable) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    ctx->tuning = enable != 0;
+    return PTYCHO_OK;
+}
+
+int ptycho_tuning(const ptycho_ctx* ctx, ptycho_tuning_info* out) {
+    if (!ctx || !out) return PTYCHO_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (!ctx->loaded) return PTYCHO_ESTATE;
+    const TuneChoice c = tune_lookup(ctx->opts.device, ctx->N, ctx->J);
+    out->tuned = ctx->tuned ? 1 : 0;
+    out->gather_rows = kGatherShape[ctx->cb.gather_shape].rows;
+    out->gather_cols = kGatherShape[ctx->cb.gather_shape].cols;
+    out->probe_ppt = ctx->cb.probe_ppt;
+    for (int s = 0; s < kGatherShapes && s < 4; ++s) out->gather_ms[s] = c.gather_ms[s];
+    out->probe_ms[0] = c.probe_ms[0];
+    out->probe_ms[1] = c.probe_ms[1];
+    out->cluster_size = ctx->divide == PTYCHO_DIVIDE_CLUSTER ? ctx->C : 0;
+    out->divide_ms[0] = c.divide_ms[0];
+    out->divide_ms[1] = c.divide_ms[1];
+    return PTYCHO_OK;
+}
+
+int ptycho_set_launch_shapes(ptycho_ctx* ctx, int32_t gather_rows, int32_t gather_cols,
+                             int32_t probe_ppt, int32_t cluster_size) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
+    int shape = -1;
+    for (int s = 0; s < kGatherShapes; ++s)
+        if (kGatherShape[s].rows == gather_rows && kGatherShape[s].cols == gather_cols) shape = s;
+    if (shape < 0 || (probe_ppt != 1 && probe_ppt != 2))
+        return fail(ctx, PTYCHO_EINVAL, "not a candidate launch shape");
+    int variant = ctx->variant;
+    if (cluster_size != 0) {
+        if (ctx->N != 128 || ctx->divide != PTYCHO_DIVIDE_CLUSTER ||
+            ctx->opts.precision != PTYCHO_PREC_FP32 || (cluster_size != 8 && cluster_size != 16))
+            return fail(ctx, PTYCHO_EINVAL, "cluster size: 8 or 16, FP32 cluster design at N = 128 only");
+        variant = cluster_size == 16 ? 1 : 0;
+    }
+    DeviceGuard dg(ctx->opts.device);
+    if (variant != ctx->variant) {
+        // sqrt(I) into the other variant's layout, through the transpose scratch
+        // (J slots of N^2 complex values hold the J N^2 floats)
+        const size_t n = (size_t)ctx->J * ctx->N * ctx->N;
+        PT_CUDA(ctx, cudaMemcpyAsync(ctx->scratch, ctx->sqrtIp, n * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+        PT_CUDA(ctx, launch_relayout_sqrt(ctx->N, ctx->variant, variant,
+                                          reinterpret_cast<const float*>(ctx->scratch), ctx->sqrtIp,
+                                          ctx->J, ctx->stream));
+        ctx->variant = variant;
+        ctx->C = divide_cluster_size(ctx->N, variant);
+    }
+    PT_CUDA(ctx, tune_apply_shape(ctx->pos_h.data(), ctx->J, ctx->N, ctx->Mr, ctx->Mc, shape, ctx->cb,
+                                  ctx->stream));
+    ctx->cb.probe_ppt = probe_ppt;
+    ctx->tuned = true;   // pinned: no tuning at the next iteration
+    return PTYCHO_OK;
+}
+
+int ptycho_set_probe_start(ptycho_ctx* ctx, int32_t start) {
+    if (!ctx) return PTYCHO_EINVAL;
+    ctx->err.clear();
+    if (start < 0) return fail(ctx, PTYCHO_EINVAL, "start must be >= 0");
+    ctx->probe_start = start;
     return PTYCHO_OK;
 }
 
@@ -610,31 +867,20 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
     ctx->err.clear();
     if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
     DeviceGuard dg(ctx->opts.device);
-    DivideArgs da{};
-    da.x = ctx->x;
-    da.y = ctx->y;
-    da.sqrtIp = ctx->sqrtIp;
-    da.P = ctx->P;
-    da.O = ctx->O;
-    da.pos = ctx->pos;
-    da.tw = ctx->tw;
-    da.e_part = ctx->e_part;
-    da.J = ctx->J;
-    da.Mc = ctx->Mc;
+    DivideArgs da = divide_args(ctx);
     da.load_x = 0;
     da.pa = 1.f;
     da.pb = 1.f;
     da.c = 1.f;
     da.write_x = 0;
     da.err_only = 1;
-    da.scratch = ctx->scratch;
-    PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
-    PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->J * ctx->C, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
+    PT_CUDA(ctx, launch_divide_ctx(ctx, da));
+    PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->n_part, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
                                   ctx->e_tmp, ctx->stream));
     PT_CUDA(ctx, cudaMemcpyAsync(fourier_err, ctx->e_tmp, sizeof(double), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return PTYCHO_OK;
+    return check_device_flags(ctx);
 }
 
 size_t ptycho_device_bytes(const ptycho_ctx* ctx) { return ctx ? ctx->bytes : 0; }
@@ -662,33 +908,23 @@ int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t 
     if (n_iter == 0) return PTYCHO_OK;
     DeviceGuard dg(ctx->opts.device);
     const double inv_sumI = ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0;
-    DivideArgs da{};
-    da.x = ctx->x;
-    da.y = ctx->y;
-    da.sqrtIp = ctx->sqrtIp;
-    da.P = ctx->P;
-    da.O = ctx->O;
+    DivideArgs da = divide_args(ctx);
     da.P_mut = ctx->P;
     da.O_mut = ctx->O;
-    da.pos = ctx->pos;
-    da.tw = ctx->tw;
-    da.e_part = ctx->e_part;
-    da.J = ctx->J;
-    da.Mc = ctx->Mc;
     da.load_x = 0;
     da.pa = 1.f;  // the exit wave P * O_j
     da.pb = 1.f;
     da.c = lam;
     da.write_x = 0;
     da.err_only = 0;
-    da.scratch = ctx->scratch;
     da.sp = 1;
+    da.lag = 1;  // one exit wave: its phases back to back
     for (int it = 0; it < n_iter; ++it) {
         for (int i = 0; i < ctx->J; ++i) {
             da.sp_pos = ord[(size_t)i];
-            PT_CUDA(ctx, launch_divide(ctx->N, da, ctx->stream));
+            PT_CUDA(ctx, launch_divide_ctx(ctx, da));
         }
-        PT_CUDA(ctx, launch_record_error(ctx->e_part, ctx->J * ctx->C, inv_sumI, ctx->e_ring,
+        PT_CUDA(ctx, launch_record_error(ctx->e_part, ctx->n_part, inv_sumI, ctx->e_ring,
                                          ctx->d_iter, kRing, ctx->stream));
         ctx->iters++;
     }

@@ -29,6 +29,7 @@
 #include "nvtx.h"
 
 using Clock = std::chrono::steady_clock;
+using namespace ptycho;
 
 namespace {
 
@@ -49,6 +50,8 @@ struct ptycho_batch {
     cudaStream_t main = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
+    int last_groups = 0;   // launch groups of the last run
+    int last_ragged = 0;   // contexts that ran in them
 };
 
 extern "C" int ptycho_batch_create(ptycho_batch** out, const ptycho_opts* opts) {
@@ -95,23 +98,133 @@ extern "C" int ptycho_batch_run(ptycho_batch* b, int32_t n_iter) {
         ~Restore() { cudaSetDevice(d); }
     } restore{prev};
 
-    // first iteration directly (contexts may start from loaded exit waves)
-    for (auto& en : b->e) {
-        int rc = ptycho_iterate(en.ctx, en.a, en.b, en.c, 1);
-        if (rc) return rc;
-    }
+    // first iteration directly (contexts may start from loaded exit waves),
+    // and directly too while any context still holds its probe fixed (the
+    // captured iteration must be the same in every replay)
+    int64_t direct = 1;
+    for (auto& en : b->e) direct = std::max<int64_t>(direct, ptycho::ctx_probe_hold(en.ctx));
+    direct = std::min<int64_t>(direct, n_iter);
+    for (int64_t k = 0; k < direct; ++k)
+        for (auto& en : b->e) {
+            int rc = ptycho_iterate(en.ctx, en.a, en.b, en.c, 1);
+            if (rc) return rc;
+        }
+    n_iter -= (int32_t)(direct - 1);  // the remaining iterations, counting the first one
     if (n_iter == 1) {
         for (auto& en : b->e)
             if (cudaStreamSynchronize(ptycho::ctx_stream(en.ctx)) != cudaSuccess) return PTYCHO_ECUDA;
         return PTYCHO_OK;
     }
-    while (b->join.size() < b->e.size()) {
+    // Launch groups: the FP32 cluster-design contexts of one pattern side (and
+    // launch variant) run each iteration as one ragged divide launch and one
+    // ragged launch per concur kernel over all their scans; the others keep a
+    // branch of their own in the graph.
+    struct Group {
+        int N = 0, variant = 0;
+        std::vector<size_t> idx;
+        cudaStream_t st = nullptr;
+        cudaEvent_t join = nullptr;
+        void* dev = nullptr;  // device tables of the group
+        RaggedConcur rc{};
+        const DivideArgs* dtab = nullptr;
+        const int* dfirst = nullptr;
+        int waves = 0;
+    };
+    const size_t ne = b->e.size();
+    std::vector<DivideArgs> das(ne);
+    std::vector<ConcurScan> css(ne);
+    std::vector<int> group_of(ne, -1);
+    std::vector<Group> groups;
+    for (size_t i = 0; i < ne; ++i) {
+        const BatchEntry& en = b->e[i];
+        int N = 0, v = 0;
+        if (!ptycho::ctx_ragged_iteration(en.ctx, en.a, en.b, en.c, &das[i], &css[i], &N, &v)) continue;
+        int g = -1;
+        for (size_t k = 0; k < groups.size(); ++k)
+            if (groups[k].N == N && groups[k].variant == v) g = (int)k;
+        if (g < 0) {
+            groups.push_back(Group{});
+            groups.back().N = N;
+            groups.back().variant = v;
+            g = (int)groups.size() - 1;
+        }
+        groups[(size_t)g].idx.push_back(i);
+        group_of[i] = g;
+    }
+    struct Cleanup {
+        std::vector<Group>* g;
+        ~Cleanup() {
+            for (Group& x : *g) {
+                if (x.st) cudaStreamDestroy(x.st);
+                if (x.join) cudaEventDestroy(x.join);
+                if (x.dev) cudaFree(x.dev);
+            }
+        }
+    } cleanup{&groups};
+    for (Group& g : groups) {
+        // one gather shape and one probe-partial width per group (a launch
+        // choice; the results do not depend on it): the first scan's
+        const ConcurBufs& c0 = css[g.idx[0]].cb;
+        for (size_t k = 1; k < g.idx.size(); ++k) {
+            const size_t i = g.idx[k];
+            if (css[i].cb.gather_shape != c0.gather_shape || css[i].cb.probe_ppt != c0.probe_ppt) {
+                const TileShape sh = kGatherShape[c0.gather_shape];
+                int rc = ptycho_set_launch_shapes(b->e[i].ctx, sh.rows, sh.cols, c0.probe_ppt, 0);
+                if (rc) return rc;
+                int N = 0, v = 0;
+                ptycho::ctx_ragged_iteration(b->e[i].ctx, b->e[i].a, b->e[i].b, b->e[i].c, &das[i],
+                                             &css[i], &N, &v);
+            }
+        }
+        const int n = (int)g.idx.size();
+        std::vector<DivideArgs> dt((size_t)n);
+        std::vector<ConcurScan> ct((size_t)n);
+        std::vector<int> wfirst((size_t)n + 1, 0);
+        for (int k = 0; k < n; ++k) {
+            dt[(size_t)k] = das[g.idx[(size_t)k]];
+            ct[(size_t)k] = css[g.idx[(size_t)k]];
+            wfirst[(size_t)k + 1] = wfirst[(size_t)k] + dt[(size_t)k].J;
+        }
+        std::vector<int> cfirst, nslice;
+        ragged_concur_tables(ct.data(), n, cfirst, nslice, g.rc.totals);
+        const size_t b_dt = dt.size() * sizeof(DivideArgs), b_ct = ct.size() * sizeof(ConcurScan);
+        const size_t b_wf = wfirst.size() * sizeof(int), b_cf = cfirst.size() * sizeof(int);
+        const size_t b_ns = nslice.size() * sizeof(int);
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const size_t total = up(b_dt) + up(b_ct) + up(b_wf) + up(b_cf) + up(b_ns);
+        if (cudaMalloc(&g.dev, total) != cudaSuccess) return PTYCHO_ENOMEM;
+        char* p = static_cast<char*>(g.dev);
+        char* p_dt = p;
+        char* p_ct = p_dt + up(b_dt);
+        char* p_wf = p_ct + up(b_ct);
+        char* p_cf = p_wf + up(b_wf);
+        char* p_ns = p_cf + up(b_cf);
+        if (cudaMemcpy(p_dt, dt.data(), b_dt, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p_ct, ct.data(), b_ct, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p_wf, wfirst.data(), b_wf, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p_cf, cfirst.data(), b_cf, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p_ns, nslice.data(), b_ns, cudaMemcpyHostToDevice) != cudaSuccess)
+            return PTYCHO_ECUDA;
+        g.dtab = reinterpret_cast<const DivideArgs*>(p_dt);
+        g.dfirst = reinterpret_cast<const int*>(p_wf);
+        g.waves = wfirst.back();
+        g.rc.scans = reinterpret_cast<const ConcurScan*>(p_ct);
+        g.rc.first = reinterpret_cast<const int*>(p_cf);
+        g.rc.n_slice = reinterpret_cast<const int*>(p_ns);
+        g.rc.n = n;
+        g.rc.gather_shape = ct[0].cb.gather_shape;
+        g.rc.probe_ppt = ct[0].cb.probe_ppt;
+        if (cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess)
+            return PTYCHO_ECUDA;
+    }
+    while (b->join.size() < ne) {
         cudaEvent_t ev;
         if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return PTYCHO_ECUDA;
         b->join.push_back(ev);
     }
-    // the main stream starts after every context's first iteration
-    for (size_t i = 0; i < b->e.size(); ++i) {
+    // the main stream starts after every context's direct iterations
+    for (size_t i = 0; i < ne; ++i) {
         if (cudaEventRecord(b->join[i], ptycho::ctx_stream(b->e[i].ctx)) != cudaSuccess ||
             cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess)
             return PTYCHO_ECUDA;
@@ -123,7 +236,16 @@ extern "C" int ptycho_batch_run(ptycho_batch* b, int32_t n_iter) {
         return PTYCHO_ECUDA;
     int rc = PTYCHO_OK;
     cudaEventRecord(b->fork, b->main);
-    for (size_t i = 0; i < b->e.size() && rc == PTYCHO_OK; ++i) {
+    for (Group& g : groups) {
+        cudaStreamWaitEvent(g.st, b->fork, 0);
+        if (launch_divide_ragged(g.N, g.variant, g.dtab, g.dfirst, g.rc.n, g.waves, g.st) != cudaSuccess ||
+            launch_concur_ragged(g.rc, g.st) != cudaSuccess)
+            rc = PTYCHO_ECUDA;
+        cudaEventRecord(g.join, g.st);
+        cudaStreamWaitEvent(b->main, g.join, 0);
+    }
+    for (size_t i = 0; i < ne && rc == PTYCHO_OK; ++i) {
+        if (group_of[i] >= 0) continue;
         cudaStream_t s = ptycho::ctx_stream(b->e[i].ctx);
         cudaStreamWaitEvent(s, b->fork, 0);
         rc = ptycho_iterate(b->e[i].ctx, b->e[i].a, b->e[i].b, b->e[i].c, 1);
@@ -144,7 +266,23 @@ extern "C" int ptycho_batch_run(ptycho_batch* b, int32_t n_iter) {
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->main);
     cudaGraphExecDestroy(exec);
     if (ce != cudaSuccess) return PTYCHO_ECUDA;
-    for (auto& en : b->e) ptycho::ctx_add_iterations(en.ctx, n_iter - 2);
+    for (size_t i = 0; i < ne; ++i) {
+        const BatchEntry& en = b->e[i];
+        if (group_of[i] >= 0)
+            ptycho::ctx_ragged_done(en.ctx, en.a, en.b, n_iter - 1);
+        else
+            ptycho::ctx_add_iterations(en.ctx, n_iter - 2);  // the capture counted one
+    }
+    b->last_groups = (int)groups.size();
+    b->last_ragged = 0;
+    for (int g : group_of) b->last_ragged += g >= 0 ? 1 : 0;
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_batch_groups(const ptycho_batch* b, int32_t* groups, int32_t* ragged) {
+    if (!b || !groups || !ragged) return PTYCHO_EINVAL;
+    *groups = b->last_groups;
+    *ragged = b->last_ragged;
     return PTYCHO_OK;
 }
 
@@ -216,7 +354,8 @@ extern "C" int ptycho_server_submit(ptycho_server* s, const ptycho_scan_desc* d,
     if (d->J < 1 || d->N < 1 || d->M_rows < d->N || d->M_cols < d->N || !d->pos_rc ||
         !d->intensity || !d->obj0 || !d->probe0)
         return PTYCHO_EINVAL;
-    const size_t need = ptycho_scan_bytes(d->J, d->N, d->M_rows, d->M_cols, s->opts.precision);
+    const size_t need = ptycho::scan_bytes(d->J, d->N, d->M_rows, d->M_cols, s->opts.precision,
+                                           s->opts.divide);
     if (need == 0 || need > s->budget) return PTYCHO_EINVAL;
     auto r = std::make_unique<Request>();
     r->id = s->next_id++;

@@ -17,11 +17,15 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libptycho.so")
+# PTYCHO_LIB=debug selects the checked build (libptycho_debug.so) for this process.
+LIB_PATH = os.path.join(_PKG, "libptycho_debug.so" if os.environ.get("PTYCHO_LIB") == "debug"
+                        else "libptycho.so")
 
 PTYCHO_OK, PTYCHO_EINVAL, PTYCHO_ENOMEM, PTYCHO_ECUDA, PTYCHO_ETIMEOUT, PTYCHO_ESTATE = 0, -1, -2, -3, -4, -5
 PTYCHO_PREC_FP32, PTYCHO_PREC_BF16X3 = 0, 1
 PTYCHO_CONCUR_DETERMINISTIC, PTYCHO_CONCUR_ATOMIC = 0, 1
+PTYCHO_DIVIDE_AUTO, PTYCHO_DIVIDE_CLUSTER, PTYCHO_DIVIDE_TWOPASS = 0, 1, 2
+DIVIDE = {"auto": PTYCHO_DIVIDE_AUTO, "cluster": PTYCHO_DIVIDE_CLUSTER, "twopass": PTYCHO_DIVIDE_TWOPASS}
 PTYCHO_LOAD_INTENSITY_DEVICE = 1
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ESTATE"}
@@ -59,7 +63,14 @@ class PtychoError(RuntimeError):
 
 class ptycho_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int), ("concur", ctypes.c_int),
-                ("alpha", ctypes.c_float), ("stream", ctypes.c_void_p)]
+                ("alpha", ctypes.c_float), ("stream", ctypes.c_void_p), ("divide", ctypes.c_int)]
+
+
+class ptycho_tuning_info(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int32), ("gather_rows", ctypes.c_int32),
+                ("gather_cols", ctypes.c_int32), ("probe_ppt", ctypes.c_int32),
+                ("gather_ms", ctypes.c_float * 4), ("probe_ms", ctypes.c_float * 2),
+                ("cluster_size", ctypes.c_int32), ("divide_ms", ctypes.c_float * 2)]
 
 
 _lib = None
@@ -89,6 +100,14 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int32)]),
     "ptycho_scan_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int]),
+    "ptycho_divide_design": (ctypes.c_int, [_P]),
+    "ptycho_set_probe_start": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "ptycho_set_tuning": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ptycho_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ptycho_tuning_info)]),
+    "ptycho_set_launch_shapes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32]),
+    "ptycho_debug_build": (ctypes.c_int, []),
+    "ptycho_debug_flags": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]),
     "ptycho_probe_update_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
                                                    _P, _P]),
@@ -242,6 +261,48 @@ def ptycho_scan_bytes(J: int, N: int, M_rows: int, M_cols: int, precision: int =
     return int(lib().ptycho_scan_bytes(J, N, M_rows, M_cols, precision))
 
 
+def ptycho_debug_build() -> bool:
+    return bool(lib().ptycho_debug_build())
+
+
+def ptycho_debug_flags(device: int = 0) -> int:
+    """Synchronise the device and read-and-clear the checked build's bits."""
+    f = ctypes.c_uint32(0)
+    rc = lib().ptycho_debug_flags(device, ctypes.byref(f))
+    if rc != PTYCHO_OK:
+        raise PtychoError(rc, "ptycho_debug_flags")
+    return int(f.value)
+
+
+def ptycho_set_tuning(h, enable: bool) -> None:
+    _check(lib().ptycho_set_tuning(h, 1 if enable else 0), h)
+
+
+def ptycho_tuning(h) -> dict:
+    t = ptycho_tuning_info()
+    _check(lib().ptycho_tuning(h, ctypes.byref(t)), h)
+    return {"tuned": bool(t.tuned), "gather_tile": (t.gather_rows, t.gather_cols),
+            "probe_pixels_per_thread": t.probe_ppt,
+            "gather_ms": {f"{r}x{c}": float(t.gather_ms[i])
+                          for i, (r, c) in enumerate(((16, 32), (8, 32), (32, 32), (8, 64)))},
+            "probe_ms": {"1": float(t.probe_ms[0]), "2": float(t.probe_ms[1])},
+            "cluster_size": t.cluster_size,
+            "divide128_ms": {"8x128": float(t.divide_ms[0]), "16x64": float(t.divide_ms[1])}}
+
+
+def ptycho_set_launch_shapes(h, gather_rows: int, gather_cols: int, probe_ppt: int,
+                             cluster_size: int = 0) -> None:
+    _check(lib().ptycho_set_launch_shapes(h, gather_rows, gather_cols, probe_ppt, cluster_size), h)
+
+
+def ptycho_set_probe_start(h, start: int) -> None:
+    _check(lib().ptycho_set_probe_start(h, start), h)
+
+
+def ptycho_divide_design(h) -> int:
+    return int(lib().ptycho_divide_design(h))
+
+
 def ptycho_probe_update_noalloc(y_dev: int, obj_dev: int, pos_dev: int, J: int, N: int,
                                 M_rows: int, M_cols: int, alpha: float, probe_out_dev: int,
                                 stream: int | None = None) -> int:
@@ -257,13 +318,14 @@ class Reconstruction:
     """One blind reconstruction held on the GPU (a ptycho_ctx)."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", concur: str = "deterministic",
-                 alpha: float = 1e-6, stream: int | None = None):
+                 alpha: float = 1e-6, stream: int | None = None, divide: str = "auto"):
         o = ptycho_default_opts()
         o.device = device
         o.precision = {"fp32": PTYCHO_PREC_FP32, "bf16x3": PTYCHO_PREC_BF16X3}[precision]
         o.concur = {"deterministic": PTYCHO_CONCUR_DETERMINISTIC, "atomic": PTYCHO_CONCUR_ATOMIC}[concur]
         o.alpha = alpha
         o.stream = stream
+        o.divide = DIVIDE[divide]
         self.h = ptycho_create(o)
         self.J = self.N = 0
         self.M_shape = (0, 0)
@@ -328,6 +390,26 @@ class Reconstruction:
     @property
     def iteration_count(self) -> int:
         return ptycho_iteration_count(self.h)
+
+    def set_tuning(self, enable: bool) -> None:
+        ptycho_set_tuning(self.h, enable)
+
+    def tuning(self) -> dict:
+        """The launch shapes the autotuner chose (and what it measured)."""
+        return ptycho_tuning(self.h)
+
+    def set_launch_shapes(self, gather_rows: int, gather_cols: int, probe_ppt: int,
+                          cluster_size: int = 0) -> None:
+        ptycho_set_launch_shapes(self.h, gather_rows, gather_cols, probe_ppt, cluster_size)
+
+    def set_probe_start(self, start: int) -> None:
+        """Hold the probe fixed in iterations k < start (k from 0 at the load)."""
+        ptycho_set_probe_start(self.h, start)
+
+    def divide_design(self) -> str:
+        """'cluster' or 'twopass': the divide design of the loaded scan."""
+        return {PTYCHO_DIVIDE_CLUSTER: "cluster", PTYCHO_DIVIDE_TWOPASS: "twopass"}.get(
+            ptycho_divide_design(self.h), "")
 
     @property
     def device_bytes(self) -> int:

@@ -30,6 +30,7 @@ _SIGS = {
     "ptycho_batch_add": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "ptycho_batch_run": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ptycho_batch_destroy": (None, [_P]),
+    "ptycho_batch_groups": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "ptycho_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_size_t, ctypes.c_int32,
                                             ctypes.POINTER(native.ptycho_opts)]),
     "ptycho_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(ptycho_scan_desc), ctypes.c_float,
@@ -79,6 +80,12 @@ def ptycho_batch_run(b: int, n_iter: int) -> None:
     _rc(lib().ptycho_batch_run(b, n_iter), "ptycho_batch_run")
 
 
+def ptycho_batch_groups(b: int) -> tuple[int, int]:
+    g, r = ctypes.c_int32(0), ctypes.c_int32(0)
+    _rc(lib().ptycho_batch_groups(b, ctypes.byref(g), ctypes.byref(r)), "ptycho_batch_groups")
+    return g.value, r.value
+
+
 def ptycho_batch_destroy(b: int) -> None:
     lib().ptycho_batch_destroy(b)
 
@@ -126,8 +133,9 @@ def ptycho_server_destroy(s: int) -> None:
 
 # --- drivers ----------------------------------------------------------------
 
-def run_batch(recons, settings, n_iter: int, device: int = 0) -> None:
-    """Advance several loaded Reconstructions together through one captured graph."""
+def run_batch(recons, settings, n_iter: int, device: int = 0) -> tuple[int, int]:
+    """Advance several loaded Reconstructions together through one captured
+    graph; returns (launch groups, contexts that ran in them)."""
     o = native.ptycho_default_opts()
     o.device = device
     b = ptycho_batch_create(o)
@@ -135,6 +143,7 @@ def run_batch(recons, settings, n_iter: int, device: int = 0) -> None:
         for r, abc in zip(recons, settings):
             ptycho_batch_add(b, r.h, *abc)
         ptycho_batch_run(b, n_iter)
+        return ptycho_batch_groups(b)
     finally:
         ptycho_batch_destroy(b)
 

@@ -1,0 +1,85 @@
+"""The probe-start reading on the GPU (ptycho_set_probe_start): the concur
+step of iterations k < start keeps the probe fixed.  Against the FP64
+oracle with the same setting (exit waves, object, probe and the per-iteration
+Fourier error; FP32 tolerance grown with the iteration count as in the other
+multi-iteration parity tests), and bitwise equal alone and in a batch whose
+captured graph starts only after every context's probe is released."""
+import numpy as np
+import pytest
+
+from oracle import ptycho as optycho
+from paper_2311_11466_gb300 import native, serve, synth
+
+from gpu_cases import rel_l2, small_spec
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2311_11466_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("name,start", [("RAAR", 3), ("DC", 2), ("DR", 5)])
+def test_probe_held_then_updated_matches_oracle(name, start):
+    s = synth.make_scan(synth.named_spec("tiny"))
+    abc = native.PRESETS[name]
+    n = 5
+    prob = optycho.Problem(s.intensity.astype(np.float64), s.pos, s.obj0.astype(np.complex128),
+                           s.probe0.astype(np.complex128), probe_start=start)
+    x = optycho.exit_waves(prob.P, prob.O, s.pos)
+    errs = []
+    for _ in range(n):
+        x = prob.iterate(x, *abc)
+        errs.append(prob.last_error)
+    with native.Reconstruction() as r:
+        r.set_probe_start(start)
+        r.load_scan(s.pos, s.intensity, s.obj0, s.probe0)
+        r.iterate(*abc, min(start, n))
+        if start <= n:
+            _, P_held = r.object_probe()
+            assert np.array_equal(P_held, s.probe0)  # untouched while held
+        r.iterate(*abc, n - min(start, n))
+        xg = r.exit_waves()
+        O, P = r.object_probe()
+        e = r.errors()
+    assert rel_l2(xg, x) <= n * TOL
+    assert rel_l2(O, prob.O) <= n * TOL
+    assert rel_l2(P, prob.P) <= n * TOL
+    np.testing.assert_allclose(e, errs, rtol=n * TOL)
+
+
+def test_set_probe_start_rejects_negative():
+    with native.Reconstruction() as r:
+        with pytest.raises(native.PtychoError):
+            r.set_probe_start(-1)
+
+
+def test_batch_with_held_probes_equals_alone():
+    scans = [synth.make_scan(small_spec(64, 3, 4, seed=31, photons=1e6)),
+             synth.make_scan(small_spec(128, 3, 3, seed=32, photons=1e6))]
+    starts = [2, 4]
+    abc = native.PRESETS["RAAR"]
+    n = 7
+    alone = []
+    for sc, k in zip(scans, starts):
+        with native.Reconstruction() as r:
+            r.set_probe_start(k)
+            r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+            r.iterate(*abc, n)
+            alone.append((r.exit_waves(), *r.object_probe(), r.errors()))
+    recons = []
+    for sc, k in zip(scans, starts):
+        r = native.Reconstruction()
+        r.set_probe_start(k)
+        r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
+        recons.append(r)
+    serve.run_batch(recons, [abc, abc], n)
+    for r, ref in zip(recons, alone):
+        got = (r.exit_waves(), *r.object_probe(), r.errors())
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b)
+        r.close()

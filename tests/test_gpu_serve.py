@@ -44,7 +44,10 @@ def test_batch_graph_equals_alone(scans):
         r = native.Reconstruction()
         r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
         recons.append(r)
-    serve.run_batch(recons, SETTINGS, n)
+    groups, ragged = serve.run_batch(recons, SETTINGS, n)
+    # every context is an FP32 cluster-design context: all of them run in the
+    # launch groups, one per pattern side (64, 128, 256)
+    assert (groups, ragged) == (3, len(scans))
     for r, sc, abc in zip(recons, scans, SETTINGS):
         x, O, P, e = _alone(sc, abc, n)
         Ob, Pb = r.object_probe()

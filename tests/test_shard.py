@@ -95,7 +95,7 @@ def test_sharded_concur_equals_single_rank_oracle():
     from oracle import ptycho as optycho
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
