@@ -123,6 +123,65 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml, read
+    only) every millisecond on a background thread, so a timed region of tens
+    of milliseconds still gets samples; `ok` is False when NVML cannot be
+    loaded (the nvidia-smi sampler then stands alone)."""
+    # public NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index: int):
+        import ctypes
+        import threading
+        self.samples = []
+        self.ok = False
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.dev)) != 0:
+                return
+            self.mx = ctypes.c_uint(0)
+            self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(self.mx))  # 1: SM clock
+            self.ok = True
+        except OSError:
+            return
+
+    def _run(self):
+        import ctypes
+        clk, rsn = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        get_r = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk)) == 0 and \
+                    get_r(self.dev, ctypes.byref(rsn)) == 0:
+                self.samples.append((clk.value, rsn.value))
+            time.sleep(0.001)
+
+    def start(self):
+        import threading
+        if self.ok:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+
+    def stop(self) -> dict | None:
+        if not self.ok or self._thread is None:
+            return None
+        self._stop.set()
+        self._thread.join(timeout=2)
+        if not self.samples:
+            return None
+        sm = [c for c, _ in self.samples]
+        reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": float(self.mx.value),
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml, 1 ms"}
+
+
 def _bf16_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -321,15 +380,21 @@ def run_batch_mode(args):
             rs.append(r)
         return rs
 
-    rs = load()
-    serve.run_batch(rs, settings, args.warmup)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    groups, ragged = serve.run_batch(rs, settings, n)
-    t_batch = time.perf_counter() - t0
-    tuning = [r.tuning() for r in rs]
-    for r in rs:
-        r.close()
+    modes = {}
+    tuning = None
+    for name, mode in (("auto", serve.PTYCHO_BATCH_AUTO), ("groups", serve.PTYCHO_BATCH_GROUPS),
+                       ("branches", serve.PTYCHO_BATCH_BRANCHES)):
+        rs = load()
+        serve.run_batch(rs, settings, args.warmup, mode=mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = serve.run_batch(rs, settings, n, mode=mode)
+        modes[name] = dict(info, value=units / (time.perf_counter() - t0))
+        if tuning is None:
+            tuning = [r.tuning() for r in rs]
+        for r in rs:
+            r.close()
+    t_batch = units / modes["auto"]["value"]
     rs = load()
     for r, abc in zip(rs, settings):
         r.iterate(*abc, args.warmup)
@@ -344,7 +409,7 @@ def run_batch_mode(args):
     line = {"metric": "position-updates/s, 16 uneven scans", "mode": "batch", "value": units / t_batch,
             "unit": UNIT, "sequential": units / t_seq, "speedup": t_seq / t_batch, "steps": n,
             "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-            "launch_groups": groups, "contexts_in_groups": ragged,
+            "modes": modes,
             "config": {"scans": [{"J": sc.J, "N": sc.N, "M": list(sc.M_shape),
                                   "geometry": sc.spec.geometry,
                                   "gather_tile": list(t["gather_tile"]),
@@ -466,13 +531,16 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
                               concur=concur, divide=divide)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
     design = r.divide_design()
+    tuning = None
     abc = native.PRESETS[preset]
     r.iterate(*abc, warmup)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
+    fine = NvmlClockSampler(local)
     if rank == 0:
         sampler.start()
+        fine.start()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -487,9 +555,15 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
         dist.barrier()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    clocks = sampler.stop() if rank == 0 else None
+    clocks = None
+    if rank == 0:
+        coarse = sampler.stop()
+        fine_rec = fine.stop()
+        # the 1 ms NVML record when there is one; the nvidia-smi record beside it
+        clocks = dict(fine_rec, nvidia_smi=coarse) if fine_rec else coarse
     native.ptycho_profile_enable(r.h, False)
     div_ms, con_ms, nrec = native.ptycho_profile_read(r.h)
+    tuning = r.tuning()
     ms = max_over_ranks(ms, torch.device("cuda", local))
     value = replica_throughput(J * steps, ws, ms / 1e3)
 
@@ -574,7 +648,7 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
     del stream
     return {"scan": scan, "value": value, "ms": ms, "abc": abc, "div_px": div_px, "roofline": roof,
             "kernel_ms_per_step": {"divide": div_ms / max(nrec, 1), "concur": con_ms / max(nrec, 1)},
-            "clocks": clocks, "e2e": e2e, "design": design}
+            "clocks": clocks, "e2e": e2e, "design": design, "tuning": tuning}
 
 
 def measure_serving(requests: int, rate: float, iters: int, max_active: int = 16,
@@ -782,6 +856,7 @@ def main():
                        "l2": "working set > L2 (no flush needed)"},
             "roofline": m["roofline"],
             "kernel_ms_per_step": m["kernel_ms_per_step"],
+            "launch_shapes": m["tuning"],
             # the survey's FFT rate: 10 N^2 log2(N^2) flops per position-update (a
             # forward and an inverse 2-D FFT at 5 N^2 log2(N^2) each), against the
             # nominal FP32 CUDA-core peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)

@@ -50,9 +50,24 @@ int ptycho_batch_add(ptycho_batch* batch, ptycho_ctx* ctx, float a, float b, flo
  * Errors: EINVAL (n_iter < 0), ESTATE (empty), ENOMEM, ECUDA. */
 int ptycho_batch_run(ptycho_batch* batch, int32_t n_iter);
 
-/* Launch groups of the last ptycho_batch_run and how many contexts ran in
- * them (the rest ran as branches of their own).  Errors: EINVAL. */
-int ptycho_batch_groups(const ptycho_batch* batch, int32_t* groups, int32_t* ragged);
+/* How a batch replays its iterations: PTYCHO_BATCH_GROUPS (launch groups, as
+ * above), PTYCHO_BATCH_BRANCHES (a graph branch per context: scans overlap
+ * across streams but each launches its own kernels), or PTYCHO_BATCH_AUTO
+ * (the default: with at least three replays, one timed replay of each and
+ * then the faster).  Both compute the same iterations, bit for bit. */
+enum { PTYCHO_BATCH_AUTO = 0, PTYCHO_BATCH_GROUPS = 1, PTYCHO_BATCH_BRANCHES = 2 };
+int ptycho_batch_set_mode(ptycho_batch* batch, int mode);  /* Errors: EINVAL. */
+
+typedef struct {
+    int32_t groups;       /* launch groups of the last run (0: none used) */
+    int32_t in_groups;    /* contexts that ran in them */
+    int32_t used;         /* the graph replayed: PTYCHO_BATCH_GROUPS or _BRANCHES */
+    float groups_ms;      /* auto mode: one timed replay of each graph (else 0) */
+    float branches_ms;
+} ptycho_batch_info_t;
+
+/* What the last ptycho_batch_run did.  Errors: EINVAL. */
+int ptycho_batch_info(const ptycho_batch* batch, ptycho_batch_info_t* out);
 
 /* Release the batch (not its contexts).  NULL is a no-op. */
 void ptycho_batch_destroy(ptycho_batch* batch);

@@ -64,23 +64,14 @@ __device__ __forceinline__ double block_max_double(double v, double* scratch) {
 // carries the position index and the window corner, so one load per window);
 // thread i owns column i % TC of rows i / TC + (kT / TC) k.  For each pixel the
 // windows covering it are added in ascending position order whatever the tile
-// shape, the numerator in FP32.  The denominator sum_j |P|^2 is carried as an
-// unevaluated pair of FP32 values (s, e) with s + e exact at every step
-// (Knuth's TwoSum: each addition's rounding error is recovered exactly and
-// accumulated in e), and the pair is combined in FP64 once per pixel at the
-// end: its final reduction is in FP64 while the loop runs on the FP32 pipe
-// (FP64 inside the loop stalls it: this part issues FP64 at a small
-// fraction of the FP32 rate).  Every tile shape therefore gives bit-identical
-// results (the shape is a pure launch choice).
-
-// s + x as s' = fl(s + x) with its exact rounding error added to e (TwoSum).
-__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
-    const float t = __fadd_rn(s, x);
-    const float xp = __fsub_rn(t, s);
-    const float sp = __fsub_rn(t, xp);
-    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, sp), __fsub_rn(x, xp)));
-    s = t;
-}
+// shape, the numerator in FP32.  The denominator sum_j |P|^2 is summed like
+// the probe's: FP32 partial sums over fixed ranges of positions (j < J/2 and
+// j >= J/2) and an FP64 final sum of the partials.  The window list is in
+// ascending position order, so the one change of range is a single list
+// entry, the same for every thread of the block; FP64 work stays out of the
+// loop (this part issues FP64 at a small fraction of the FP32 rate).  Every
+// tile shape therefore gives bit-identical results (the shape is a pure
+// launch choice).
 
 constexpr int kListStage = 256;  // window-list entries staged in shared memory at a time
 
@@ -100,56 +91,114 @@ __device__ __forceinline__ void gather_body(const ConcurScan& cs, const int tile
     const float2* __restrict__ P = cs.P;
     const int4* __restrict__ tile_win = cs.cb.tile_win;
     float2 acc[KP];
-    float ds[KP], de[KP];   // denominator: sum and accumulated rounding errors
+    float dg[KP];           // denominator: FP32 partial of the current position range
+    double dd[KP];          // and the FP64 total of the ranges done
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
         acc[k] = make_float2(0.f, 0.f);
-        ds[k] = 0.f;
-        de[k] = 0.f;
+        dg[k] = 0.f;
+        dd[k] = 0.0;
     }
     const size_t NN = (size_t)N * N;
     const int l0 = cs.cb.tile_ptr[tile], l1 = cs.cb.tile_ptr[tile + 1];
-    // The tile's window list is staged in shared memory (kListStage entries at
-    // a time), so the loads of y and P depend on a shared-memory load rather
-    // than on a global one; deep unrolling keeps several windows in flight.
-    __shared__ int4 list[kListStage];
-    for (int b0 = l0; b0 < l1; b0 += kListStage) {
-    const int nb = min(kListStage, l1 - b0);
-    __syncthreads();  // the previous batch is consumed
-    for (int i = threadIdx.x; i < nb; i += kT) list[i] = __ldg(tile_win + b0 + i);
-    __syncthreads();
-#pragma unroll(KP >= 8 ? 1 : 8 / KP)
-    for (int l = 0; l < nb; ++l) {
-        const int4 w = list[l];  // (position j, row, col) of the window
-#if PT_DBG_ENABLED
-        // checked build: an entry whose window leaves the object is recorded and skipped
-        if (w.x < 0 || w.y < 0 || w.z < 0 || w.y > Mr - N || w.z > Mc - N) {
-            if (threadIdx.x == 0) PT_DBG_FLAG(kDbgWindow);
-            continue;
-        }
-#endif
-        const int cc = mc - w.z;
-        const bool cin = (unsigned)cc < (unsigned)N;
-        const float2* yj = y + (size_t)w.x * NN;
+    const int js = cs.J / 2;   // first position of the second range
+    // The windows of one range of list entries, added for every pixel of this
+    // thread in list order.  Windows go in groups of kGroup: the loads of a
+    // whole group are issued before its arithmetic, so several windows' y and
+    // P are in flight at once (a window that misses a pixel loads P[0] and no y).
+    auto add_one = [&](const int4 w, const int k, float2 pv, float2 yv) {
+        (void)w;
+        acc[k] = cadd(acc[k], cconjmul(pv, yv));
+        dg[k] += cabs2(pv);
+    };
+    auto add_range = [&](const int4* ent, int n) {
+        constexpr int kGroup = 4;
+        int l = 0;
+        for (; l + kGroup <= n; l += kGroup) {
+            float2 pv[kGroup][KP], yv[kGroup][KP];
+            bool ok[kGroup][KP];
 #pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const int rr = mr0 + TRG * k - w.y;
-            if (cin && (unsigned)rr < (unsigned)N) {
-                const int o = rr * N + cc;
-                const float2 pv = __ldg(P + o);
-                const float2 yv = __ldcs(yj + o);
-                acc[k] = cadd(acc[k], cconjmul(pv, yv));
-                two_sum_acc(ds[k], de[k], cabs2(pv));
+            for (int g = 0; g < kGroup; ++g) {
+                const int4 w = ent[l + g];  // (position j, row, col) of the window
+                const int cc = mc - w.z;
+                const bool cin = (unsigned)cc < (unsigned)N;
+                const float2* yj = y + (size_t)w.x * NN;
+#pragma unroll
+                for (int k = 0; k < KP; ++k) {
+                    const int rr = mr0 + TRG * k - w.y;
+                    ok[g][k] = cin && (unsigned)rr < (unsigned)N;
+                    const int o = ok[g][k] ? rr * N + cc : 0;
+                    pv[g][k] = __ldg(P + o);
+                    yv[g][k] = ok[g][k] ? __ldcs(yj + o) : make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+                for (int k = 0; k < KP; ++k)
+                    if (ok[g][k]) add_one(ent[l + g], k, pv[g][k], yv[g][k]);
+        }
+        for (; l < n; ++l) {
+            const int4 w = ent[l];
+            const int cc = mc - w.z;
+            const bool cin = (unsigned)cc < (unsigned)N;
+            const float2* yj = y + (size_t)w.x * NN;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int rr = mr0 + TRG * k - w.y;
+                if (cin && (unsigned)rr < (unsigned)N) {
+                    const int o = rr * N + cc;
+                    add_one(w, k, __ldg(P + o), __ldcs(yj + o));
+                }
             }
         }
-    }
+    };
+    // The tile's window list is staged in shared memory (kListStage entries at
+    // a time), so the loads of y and P depend on a shared-memory load rather
+    // than on a global one.  The list is in ascending position order: each
+    // batch splits into the entries of the first position range and those of
+    // the second (a binary search, the same for every thread), and the
+    // denominator's FP32 partial moves to FP64 once, between the two.
+    __shared__ int4 list[kListStage];
+    bool second = false;
+    for (int b0 = l0; b0 < l1; b0 += kListStage) {
+        const int nb = min(kListStage, l1 - b0);
+        __syncthreads();  // the previous batch is consumed
+        for (int i = threadIdx.x; i < nb; i += kT) {
+            int4 w = __ldg(tile_win + b0 + i);
+#if PT_DBG_ENABLED
+            // checked build: an entry whose window leaves the object is recorded
+            // and replaced by one that covers no pixel of the tile
+            if (w.x < 0 || w.y < 0 || w.z < 0 || w.y > Mr - N || w.z > Mc - N) {
+                PT_DBG_FLAG(kDbgWindow);
+                w = make_int4(0, -2 * N, -2 * N, 0);
+            }
+#endif
+            list[i] = w;
+        }
+        __syncthreads();
+        int lo = 0, hi = nb;   // first entry of the batch with position >= js
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (list[mid].x < js) lo = mid + 1; else hi = mid;
+        }
+        add_range(list, lo);
+        if (!second && lo < nb) {
+            second = true;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                dd[k] = (double)dg[k];
+                dg[k] = 0.f;
+            }
+        }
+        add_range(list + lo, nb - lo);
     }
     unsigned long long mx = 0ull;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
         const int mr = mr0 + TRG * k;
         if (mr < Mr && mc < Mc) {
-            const double den = (double)ds[k] + (double)de[k];   // the final reduction, FP64
+            const double den = dd[k] + (double)dg[k];   // the final sum, FP64
             cs.cb.numO[(size_t)mr * Mc + mc] = acc[k];
             cs.cb.denO[(size_t)mr * Mc + mc] = den;
             const unsigned long long b = (unsigned long long)__double_as_longlong(den);
@@ -213,9 +262,8 @@ __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, c
     static_assert(PPT == 1 || PPT == 2, "pixels per thread");
     const int N = cs.N, Mc = cs.Mc, J = cs.J, chunks = cs.cb.chunks;
     const int r = (bx * kT + threadIdx.x) * PPT;
-    // N is even, so with PPT = 2 both pixels of a thread are inside or both out;
-    // threads past the last pixel still take part in the staging below
-    const int rr = r < N * N ? r / N : 0, cc = r < N * N ? r % N : 0;
+    if (r >= N * N) return;   // N is even, so with PPT = 2 both pixels are inside
+    const int rr = r / N, cc = r % N;
     const int j0 = (int)(((long)ch * J) / chunks), j1 = (int)(((long)(ch + 1) * J) / chunks);
     const size_t NN = (size_t)N * N;
     const float2* __restrict__ y = cs.y;
@@ -228,19 +276,9 @@ __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, c
         acc[i] = make_float2(0.f, 0.f);
         den[i] = 0.f;
     }
-    // the chunk's positions staged in shared memory (every thread of the block
-    // takes part in the staging, including those past the last pixel)
-    __shared__ int2 spos[kListStage];
-    for (int b0 = j0; b0 < j1; b0 += kListStage) {
-    const int nb = min(kListStage, j1 - b0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += kT) spos[i] = pos[b0 + i];
-    __syncthreads();
-    if (r < N * N) {
 #pragma unroll 4
-    for (int jj = 0; jj < nb; ++jj) {
-        const int j = b0 + jj;
-        const int2 s = spos[jj];
+    for (int j = j0; j < j1; ++j) {
+        const int2 s = pos[j];
 #if PT_DBG_ENABLED
         // checked build: a window outside the object is recorded and skipped
         if (s.x < 0 || s.y < 0 || s.x > cs.Mr - N || s.y > Mc - N) {
@@ -264,9 +302,6 @@ __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, c
             den[i] += cabs2(ov);
         }
     }
-    }
-    }
-    if (r >= N * N) return;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
         cs.cb.partP[(size_t)ch * NN + r + i] = acc[i];
@@ -434,6 +469,18 @@ __global__ void __launch_bounds__(kT) ragged_pnorm_kernel(const ConcurScan* __re
     pnorm_body(scans[s], blockIdx.x - first[s], n_slice[s]);
 }
 
+// Stage 1 of a two-level sum: block b adds the contiguous slice b of parts.
+__global__ void __launch_bounds__(kT) slice_sums_kernel(const double* __restrict__ parts, int n,
+                                                        double* __restrict__ out) {
+    __shared__ double scratch[kT / 32];
+    const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int e0 = (int)blockIdx.x * per, e1 = min(n, e0 + per);
+    double s = 0.0;
+    for (int i = e0 + (int)threadIdx.x; i < e1; i += kT) s += parts[i];
+    const double tot = block_sum_double<kT>(s, scratch);
+    if (threadIdx.x == 0) out[blockIdx.x] = tot;
+}
+
 __global__ void __launch_bounds__(kT) sum_parts_kernel(const double* __restrict__ parts, int n,
                                                        double scale, double* __restrict__ out) {
     __shared__ double scratch[kT / 32];
@@ -585,9 +632,13 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
     object_normalise_kernel<<<(unsigned)((M + kT - 1) / kT), kT, 0, st>>>(cs);
     if (!update_probe) {
         // the probe is held: the iteration's Fourier error from the divide
-        // kernel's partials, and the object maximum cleared for the next gather
-        record_error_kernel<<<1, kT, 0, st>>>(cs.e_part, cs.n_part, cs.inv_sumI, cs.e_ring,
-                                              cs.d_iter, cs.ring_cap);
+        // kernel's partials (slices summed into the probe-reduce slice buffer,
+        // unused in this iteration), and the object maximum cleared for the
+        // next gather
+        const int nb = probe_reduce_blocks(cs.N, cb.chunks);
+        slice_sums_kernel<<<nb, kT, 0, st>>>(cs.e_part, cs.n_part, cb.e_slice);
+        record_error_kernel<<<1, kT, 0, st>>>(cb.e_slice, nb, cs.inv_sumI, cs.e_ring, cs.d_iter,
+                                              cs.ring_cap);
         cudaMemsetAsync(cb.maxO, 0, sizeof(unsigned long long), st);
         return cudaGetLastError();
     }
@@ -642,9 +693,19 @@ cudaError_t launch_concur_ragged(const RaggedConcur& rc, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Many partials are summed in two levels (fixed slices, then the slice
+// totals in order) so the single final block has little to add.
+constexpr int kSliceBlocks = 256;
+
 cudaError_t launch_record_error(const double* parts, int n, double scale, double* ring,
-                                unsigned long long* d_iter, int cap, cudaStream_t st) {
-    record_error_kernel<<<1, kT, 0, st>>>(parts, n, scale, ring, d_iter, cap);
+                                unsigned long long* d_iter, int cap, double* scratch,
+                                cudaStream_t st) {
+    if (n > 16 * kT) {
+        slice_sums_kernel<<<kSliceBlocks, kT, 0, st>>>(parts, n, scratch);
+        record_error_kernel<<<1, kT, 0, st>>>(scratch, kSliceBlocks, scale, ring, d_iter, cap);
+    } else {
+        record_error_kernel<<<1, kT, 0, st>>>(parts, n, scale, ring, d_iter, cap);
+    }
     return cudaGetLastError();
 }
 
@@ -663,8 +724,13 @@ cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, cons
 }
 
 cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
-                             cudaStream_t st) {
-    sum_parts_kernel<<<1, kT, 0, st>>>(parts, n, scale, out);
+                             double* scratch, cudaStream_t st) {
+    if (n > 16 * kT) {
+        slice_sums_kernel<<<kSliceBlocks, kT, 0, st>>>(parts, n, scratch);
+        sum_parts_kernel<<<1, kT, 0, st>>>(scratch, kSliceBlocks, scale, out);
+    } else {
+        sum_parts_kernel<<<1, kT, 0, st>>>(parts, n, scale, out);
+    }
     return cudaGetLastError();
 }
 

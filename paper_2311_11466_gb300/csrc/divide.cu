@@ -98,7 +98,7 @@ enum : int { kModeDivide = 0, kModeErrOnly = 1, kModeSP = 2 };
 
 // The work of one CTA of the cluster that handles exit wave j.
 template <int N, int MODE, int V>
-__device__ __forceinline__ void divide_body(const DivideArgs& args, const int j) {
+__device__ __forceinline__ void divide_body(const DivideArgs args, const int j) {
     constexpr bool ERR_ONLY = MODE == kModeErrOnly;
     constexpr bool SP = MODE == kModeSP;
     using G = Geo<N, V>;

@@ -157,11 +157,15 @@ cudaError_t launch_form_waves(float2* x, const float2* P, const float2* O, const
 cudaError_t launch_materialise(float2* x, const float2* y, const float2* P, const float2* O,
                                const int2* pos, int J, int N, int Mc, float pa, float pb,
                                cudaStream_t st);
+
+// FP64 sum of parts times scale into *out (scratch: 256 doubles for the
+// slice totals of a long list).
 cudaError_t launch_sum_parts(const double* parts, int n, double scale, double* out,
-                             cudaStream_t st);
+                             double* scratch, cudaStream_t st);
 // FP64 sum of parts times scale into ring[*d_iter % cap], then ++*d_iter.
 cudaError_t launch_record_error(const double* parts, int n, double scale, double* ring,
-                                unsigned long long* d_iter, int cap, cudaStream_t st);
+                                unsigned long long* d_iter, int cap, double* scratch,
+                                cudaStream_t st);
 
 // Tensor-core (BF16 x 3) divide path (dft_gemm.cu).
 bool bf16x3_supported(int N);
@@ -218,7 +222,9 @@ int64_t ctx_probe_hold(const ptycho_ctx* ctx);
 // *N and *variant give the launch group.
 bool ctx_ragged_iteration(ptycho_ctx* ctx, float a, float b, float c, DivideArgs* da,
                           ConcurScan* cs, int* N, int* variant);
-// Account n iterations of the context that ran in batched launches.
-void ctx_ragged_done(ptycho_ctx* ctx, float a, float b, int64_t n);
+// After iterations with (a, b) that ran in a replayed graph: the context's
+// host-side state, and its iteration count set to n.
+void ctx_batch_done(ptycho_ctx* ctx, float a, float b, int64_t n);
+int64_t ctx_iterations(const ptycho_ctx* ctx);
 
 }  // namespace ptycho

@@ -66,7 +66,7 @@ struct ptycho_ctx {
     std::vector<void*> allocs;
     size_t bytes = 0;
 
-    bool have_x = true;
+    bool have_x = true;    // x_k is in the x buffer (else x_k = re-split(pa, pb), see above)
     float pa = 1.f, pb = 1.f;
     int64_t iters = 0;
     int32_t probe_start = 0;  // iterations k < probe_start hold the probe fixed
@@ -231,6 +231,27 @@ int materialise(ptycho_ctx* ctx) {
     return PTYCHO_OK;
 }
 
+// The divide arguments of the context's next iteration with (a, b, c), from
+// its lazy state.
+DivideArgs iteration_args(ptycho_ctx* ctx, float a, float b, float c) {
+    DivideArgs da = divide_args(ctx);
+    da.load_x = ctx->have_x ? 1 : 0;
+    da.pa = ctx->pa;
+    da.pb = ctx->pb;
+    da.c = c;
+    da.err_only = 0;
+    da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;  // x_k is the next (1 - a) term
+    (void)b;
+    return da;
+}
+
+// The host-side lazy state after an iteration with (a, b).
+void iteration_done(ptycho_ctx* ctx, float a, float b) {
+    ctx->have_x = false;
+    ctx->pa = a;
+    ctx->pb = b;
+}
+
 }  // namespace
 
 namespace ptycho {
@@ -244,27 +265,19 @@ bool ctx_ragged_iteration(ptycho_ctx* ctx, float a, float b, float c, DivideArgs
         ctx->divide != PTYCHO_DIVIDE_CLUSTER || ctx->opts.concur != PTYCHO_CONCUR_DETERMINISTIC ||
         ctx->iters < ctx->probe_start || !ctx->tuned)
         return false;
-    *da = divide_args(ctx);
-    da->load_x = 0;
-    da->pa = ctx->pa;
-    da->pb = ctx->pb;
-    da->c = c;
-    da->write_x = a != 1.0f ? 1 : 0;
-    da->err_only = 0;
+    *da = iteration_args(ctx, a, b, c);
     *cs = concur_scan(ctx, ctx->n_part);
     *N = ctx->N;
     *variant = ctx->variant;
-    (void)b;
     return true;
 }
 
-void ctx_ragged_done(ptycho_ctx* ctx, float a, float b, int64_t n) {
-    if (n <= 0) return;
-    ctx->have_x = false;
-    ctx->pa = a;
-    ctx->pb = b;
-    ctx->iters += n;
+void ctx_batch_done(ptycho_ctx* ctx, float a, float b, int64_t n) {
+    iteration_done(ctx, a, b);
+    ctx->iters = n;
 }
+
+int64_t ctx_iterations(const ptycho_ctx* ctx) { return ctx->iters; }
 
 int64_t ctx_probe_hold(const ptycho_ctx* ctx) {
     return ctx->iters < ctx->probe_start ? ctx->probe_start - ctx->iters : 0;
@@ -378,7 +391,7 @@ size_t ptycho::scan_bytes(int J, int N, int M_rows, int M_cols, int precision, i
     b += 2 * NN * sizeof(float2) + M * sizeof(float2);  // P, tw, O
     b += (size_t)J * sizeof(int2);
     const size_t parts_fp32 = (size_t)J * (N > 16 ? N : 16);  // either divide design
-    b += parts_fp32 * sizeof(double) + (size_t)kRing * sizeof(double) + 64;
+    b += parts_fp32 * sizeof(double) + (size_t)kRing * sizeof(double) + 64 + 256 * sizeof(double);
     b += M * (sizeof(float2) + sizeof(double)) + 16;
     b += chunks * NN * (sizeof(float2) + sizeof(float));
     b += NN * (sizeof(double2) + sizeof(double));
@@ -481,7 +494,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     const size_t parts_fp32 = (size_t)J * (N > 16 ? N : 16);  // either divide design
     PT_ALLOC(ctx->e_part, parts_fp32);
     PT_ALLOC(ctx->e_ring, (size_t)kRing);
-    PT_ALLOC(ctx->e_tmp, (size_t)4);
+    PT_ALLOC(ctx->e_tmp, (size_t)4 + 256);  // [0]: a result; [4..]: slice totals
     PT_ALLOC(ctx->d_iter, (size_t)1);
     PT_ALLOC(ctx->dflag, (size_t)4);
     PT_ALLOC(ctx->cb.numO, M);
@@ -641,13 +654,7 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
     if (!ctx->loaded) return fail(ctx, PTYCHO_ESTATE, "no scan loaded");
     DeviceGuard dg(ctx->opts.device);
     for (int it = 0; it < n_iter; ++it) {
-        DivideArgs da = divide_args(ctx);
-        da.load_x = ctx->have_x ? 1 : 0;
-        da.pa = ctx->pa;
-        da.pb = ctx->pb;
-        da.c = c;
-        da.write_x = (!ctx->have_x && a != 1.0f) ? 1 : 0;
-        da.err_only = 0;
+        DivideArgs da = iteration_args(ctx, a, b, c);
         const bool rec = ctx->prof && ctx->prof_n < kProfMax;
         if (rec) PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n], ctx->stream));
         int n_part = ctx->n_part;
@@ -678,9 +685,7 @@ int ptycho_iterate(ptycho_ctx* ctx, float a, float b, float c, int32_t n_iter) {
             PT_CUDA(ctx, cudaEventRecord(ctx->ev[3 * ctx->prof_n + 2], ctx->stream));
             ctx->prof_n++;
         }
-        ctx->have_x = false;
-        ctx->pa = a;
-        ctx->pb = b;
+        iteration_done(ctx, a, b);
         ctx->iters++;
     }
     return PTYCHO_OK;
@@ -876,7 +881,7 @@ int ptycho_model_error(ptycho_ctx* ctx, double* fourier_err) {
     da.err_only = 1;
     PT_CUDA(ctx, launch_divide_ctx(ctx, da));
     PT_CUDA(ctx, launch_sum_parts(ctx->e_part, ctx->n_part, ctx->sumI > 0 ? 1.0 / ctx->sumI : 1.0,
-                                  ctx->e_tmp, ctx->stream));
+                                  ctx->e_tmp, ctx->e_tmp + 4, ctx->stream));
     PT_CUDA(ctx, cudaMemcpyAsync(fourier_err, ctx->e_tmp, sizeof(double), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -925,7 +930,7 @@ int ptycho_sp_iterate(ptycho_ctx* ctx, float lam, const int32_t* order, int32_t 
             PT_CUDA(ctx, launch_divide_ctx(ctx, da));
         }
         PT_CUDA(ctx, launch_record_error(ctx->e_part, ctx->n_part, inv_sumI, ctx->e_ring,
-                                         ctx->d_iter, kRing, ctx->stream));
+                                         ctx->d_iter, kRing, ctx->e_tmp + 4, ctx->stream));
         ctx->iters++;
     }
     // the product-space iterate follows the new object and probe

@@ -50,8 +50,8 @@ struct ptycho_batch {
     cudaStream_t main = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
-    int last_groups = 0;   // launch groups of the last run
-    int last_ragged = 0;   // contexts that ran in them
+    int mode = PTYCHO_BATCH_AUTO;
+    ptycho_batch_info_t info{};  // of the last run
 };
 
 extern "C" int ptycho_batch_create(ptycho_batch** out, const ptycho_opts* opts) {
@@ -229,60 +229,111 @@ extern "C" int ptycho_batch_run(ptycho_batch* b, int32_t n_iter) {
             cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess)
             return PTYCHO_ECUDA;
     }
-    // capture one steady-state iteration of every context
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return PTYCHO_ECUDA;
+    // Capture one steady-state iteration of every context: with launch groups
+    // (groups, plus branches for the other contexts), and with a branch per
+    // context.  Both compute the same iteration, bit for bit.
+    std::vector<int64_t> base(ne);
+    for (size_t i = 0; i < ne; ++i) base[i] = ptycho::ctx_iterations(b->e[i].ctx);
+    auto capture = [&](bool use_groups, cudaGraphExec_t* exec) -> int {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return PTYCHO_ECUDA;
+        int rc = PTYCHO_OK;
+        cudaEventRecord(b->fork, b->main);
+        if (use_groups) {
+            for (Group& g : groups) {
+                cudaStreamWaitEvent(g.st, b->fork, 0);
+                if (launch_divide_ragged(g.N, g.variant, g.dtab, g.dfirst, g.rc.n, g.waves, g.st) !=
+                        cudaSuccess ||
+                    launch_concur_ragged(g.rc, g.st) != cudaSuccess)
+                    rc = PTYCHO_ECUDA;
+                cudaEventRecord(g.join, g.st);
+                cudaStreamWaitEvent(b->main, g.join, 0);
+            }
+        }
+        for (size_t i = 0; i < ne && rc == PTYCHO_OK; ++i) {
+            if (use_groups && group_of[i] >= 0) continue;
+            cudaStream_t s = ptycho::ctx_stream(b->e[i].ctx);
+            cudaStreamWaitEvent(s, b->fork, 0);
+            rc = ptycho_iterate(b->e[i].ctx, b->e[i].a, b->e[i].b, b->e[i].c, 1);
+            cudaEventRecord(b->join[i], s);
+            cudaStreamWaitEvent(b->main, b->join[i], 0);
+        }
+        cudaError_t ce = cudaStreamEndCapture(b->main, &graph);
+        if (rc != PTYCHO_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != PTYCHO_OK ? rc : PTYCHO_ECUDA;
+        }
+        ce = cudaGraphInstantiate(exec, graph, 0);
+        cudaGraphDestroy(graph);
+        return ce == cudaSuccess ? PTYCHO_OK : PTYCHO_ECUDA;
+    };
+    const bool have_groups = !groups.empty() && b->mode != PTYCHO_BATCH_BRANCHES;
+    const bool try_both = have_groups && b->mode == PTYCHO_BATCH_AUTO && n_iter - 1 >= 3;
+    cudaGraphExec_t gexec = nullptr, bexec = nullptr;
+    struct ExecGuard {
+        cudaGraphExec_t* a;
+        cudaGraphExec_t* b;
+        ~ExecGuard() {
+            if (*a) cudaGraphExecDestroy(*a);
+            if (*b) cudaGraphExecDestroy(*b);
+        }
+    } exec_guard{&gexec, &bexec};
     int rc = PTYCHO_OK;
-    cudaEventRecord(b->fork, b->main);
-    for (Group& g : groups) {
-        cudaStreamWaitEvent(g.st, b->fork, 0);
-        if (launch_divide_ragged(g.N, g.variant, g.dtab, g.dfirst, g.rc.n, g.waves, g.st) != cudaSuccess ||
-            launch_concur_ragged(g.rc, g.st) != cudaSuccess)
-            rc = PTYCHO_ECUDA;
-        cudaEventRecord(g.join, g.st);
-        cudaStreamWaitEvent(b->main, g.join, 0);
-    }
-    for (size_t i = 0; i < ne && rc == PTYCHO_OK; ++i) {
-        if (group_of[i] >= 0) continue;
-        cudaStream_t s = ptycho::ctx_stream(b->e[i].ctx);
-        cudaStreamWaitEvent(s, b->fork, 0);
-        rc = ptycho_iterate(b->e[i].ctx, b->e[i].a, b->e[i].b, b->e[i].c, 1);
-        cudaEventRecord(b->join[i], s);
-        cudaStreamWaitEvent(b->main, b->join[i], 0);
-    }
-    cudaError_t ce = cudaStreamEndCapture(b->main, &graph);
-    if (rc != PTYCHO_OK || ce != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc != PTYCHO_OK ? rc : PTYCHO_ECUDA;
-    }
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return PTYCHO_ECUDA;
-    // the capture recorded one iteration per context without running it;
+    if (have_groups && (rc = capture(true, &gexec)) != PTYCHO_OK) return rc;
+    if ((!have_groups || try_both) && (rc = capture(false, &bexec)) != PTYCHO_OK) return rc;
+    // the captures recorded one iteration per context without running it;
     // n_iter - 1 replays run iterations 2 .. n_iter
-    for (int it = 1; it < n_iter && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(exec, b->main);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->main);
-    cudaGraphExecDestroy(exec);
-    if (ce != cudaSuccess) return PTYCHO_ECUDA;
-    for (size_t i = 0; i < ne; ++i) {
-        const BatchEntry& en = b->e[i];
-        if (group_of[i] >= 0)
-            ptycho::ctx_ragged_done(en.ctx, en.a, en.b, n_iter - 1);
-        else
-            ptycho::ctx_add_iterations(en.ctx, n_iter - 2);  // the capture counted one
+    int replays = n_iter - 1;
+    cudaError_t ce = cudaSuccess;
+    b->info = ptycho_batch_info_t{};
+    cudaGraphExec_t use = have_groups ? gexec : bexec;
+    if (try_both) {
+        // one timed replay of each, then the faster one for the rest
+        cudaEvent_t e0, e1, e2;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventCreate(&e2);
+        cudaEventRecord(e0, b->main);
+        ce = cudaGraphLaunch(gexec, b->main);
+        cudaEventRecord(e1, b->main);
+        if (ce == cudaSuccess) ce = cudaGraphLaunch(bexec, b->main);
+        cudaEventRecord(e2, b->main);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e2);
+        float tg = 0.f, tb = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tg, e0, e1);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&tb, e1, e2);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        if (ce != cudaSuccess) return PTYCHO_ECUDA;
+        b->info.groups_ms = tg;
+        b->info.branches_ms = tb;
+        use = tg <= tb ? gexec : bexec;
+        replays -= 2;
     }
-    b->last_groups = (int)groups.size();
-    b->last_ragged = 0;
-    for (int g : group_of) b->last_ragged += g >= 0 ? 1 : 0;
+    for (int it = 0; it < replays && ce == cudaSuccess; ++it) ce = cudaGraphLaunch(use, b->main);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->main);
+    if (ce != cudaSuccess) return PTYCHO_ECUDA;
+    for (size_t i = 0; i < ne; ++i)
+        ptycho::ctx_batch_done(b->e[i].ctx, b->e[i].a, b->e[i].b, base[i] + (n_iter - 1));
+    b->info.groups = have_groups ? (int32_t)groups.size() : 0;
+    int32_t in = 0;
+    for (int g : group_of) in += (have_groups && g >= 0) ? 1 : 0;
+    b->info.in_groups = in;
+    b->info.used = use == gexec && have_groups ? PTYCHO_BATCH_GROUPS : PTYCHO_BATCH_BRANCHES;
     return PTYCHO_OK;
 }
 
-extern "C" int ptycho_batch_groups(const ptycho_batch* b, int32_t* groups, int32_t* ragged) {
-    if (!b || !groups || !ragged) return PTYCHO_EINVAL;
-    *groups = b->last_groups;
-    *ragged = b->last_ragged;
+extern "C" int ptycho_batch_set_mode(ptycho_batch* b, int mode) {
+    if (!b || mode < PTYCHO_BATCH_AUTO || mode > PTYCHO_BATCH_BRANCHES) return PTYCHO_EINVAL;
+    b->mode = mode;
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_batch_info(const ptycho_batch* b, ptycho_batch_info_t* out) {
+    if (!b || !out) return PTYCHO_EINVAL;
+    *out = b->info;
     return PTYCHO_OK;
 }
 

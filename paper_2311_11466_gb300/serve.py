@@ -30,7 +30,8 @@ _SIGS = {
     "ptycho_batch_add": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "ptycho_batch_run": (ctypes.c_int, [_P, ctypes.c_int32]),
     "ptycho_batch_destroy": (None, [_P]),
-    "ptycho_batch_groups": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "ptycho_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ptycho_batch_info": (ctypes.c_int, [_P, ctypes.c_void_p]),
     "ptycho_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_size_t, ctypes.c_int32,
                                             ctypes.POINTER(native.ptycho_opts)]),
     "ptycho_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(ptycho_scan_desc), ctypes.c_float,
@@ -80,10 +81,24 @@ def ptycho_batch_run(b: int, n_iter: int) -> None:
     _rc(lib().ptycho_batch_run(b, n_iter), "ptycho_batch_run")
 
 
-def ptycho_batch_groups(b: int) -> tuple[int, int]:
-    g, r = ctypes.c_int32(0), ctypes.c_int32(0)
-    _rc(lib().ptycho_batch_groups(b, ctypes.byref(g), ctypes.byref(r)), "ptycho_batch_groups")
-    return g.value, r.value
+PTYCHO_BATCH_AUTO, PTYCHO_BATCH_GROUPS, PTYCHO_BATCH_BRANCHES = 0, 1, 2
+
+
+class ptycho_batch_info_t(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int32), ("in_groups", ctypes.c_int32), ("used", ctypes.c_int32),
+                ("groups_ms", ctypes.c_float), ("branches_ms", ctypes.c_float)]
+
+
+def ptycho_batch_set_mode(b: int, mode: int) -> None:
+    _rc(lib().ptycho_batch_set_mode(b, mode), "ptycho_batch_set_mode")
+
+
+def ptycho_batch_info(b: int) -> dict:
+    t = ptycho_batch_info_t()
+    _rc(lib().ptycho_batch_info(b, ctypes.addressof(t)), "ptycho_batch_info")
+    return {"groups": t.groups, "in_groups": t.in_groups,
+            "used": {1: "groups", 2: "branches"}.get(t.used, ""),
+            "groups_ms": float(t.groups_ms), "branches_ms": float(t.branches_ms)}
 
 
 def ptycho_batch_destroy(b: int) -> None:
@@ -133,17 +148,18 @@ def ptycho_server_destroy(s: int) -> None:
 
 # --- drivers ----------------------------------------------------------------
 
-def run_batch(recons, settings, n_iter: int, device: int = 0) -> tuple[int, int]:
+def run_batch(recons, settings, n_iter: int, device: int = 0, mode: int = PTYCHO_BATCH_AUTO) -> dict:
     """Advance several loaded Reconstructions together through one captured
-    graph; returns (launch groups, contexts that ran in them)."""
+    graph; returns what the batch did (ptycho_batch_info)."""
     o = native.ptycho_default_opts()
     o.device = device
     b = ptycho_batch_create(o)
     try:
+        ptycho_batch_set_mode(b, mode)
         for r, abc in zip(recons, settings):
             ptycho_batch_add(b, r.h, *abc)
         ptycho_batch_run(b, n_iter)
-        return ptycho_batch_groups(b)
+        return ptycho_batch_info(b)
     finally:
         ptycho_batch_destroy(b)
 

@@ -1,8 +1,8 @@
 """The probe-start reading on the GPU (ptycho_set_probe_start): the concur
 step of iterations k < start keeps the probe fixed.  Against the FP64
 oracle with the same setting (exit waves, object, probe and the per-iteration
-Fourier error; FP32 tolerance grown with the iteration count as in the other
-multi-iteration parity tests), and bitwise equal alone and in a batch whose
+Fourier error; FP32 tolerance grown with the iteration count, or the oracle's
+own conditioning where that is wider, as in the other multi-iteration tests), and bitwise equal alone and in a batch whose
 captured graph starts only after every context's probe is released."""
 import numpy as np
 import pytest
@@ -10,7 +10,7 @@ import pytest
 from oracle import ptycho as optycho
 from paper_2311_11466_gb300 import native, serve, synth
 
-from gpu_cases import rel_l2, small_spec
+from gpu_cases import conditioned_tol, oracle_sensitivity, rel_l2, small_spec
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +46,12 @@ def test_probe_held_then_updated_matches_oracle(name, start):
         xg = r.exit_waves()
         O, P = r.object_probe()
         e = r.errors()
-    assert rel_l2(xg, x) <= n * TOL
-    assert rel_l2(O, prob.O) <= n * TOL
-    assert rel_l2(P, prob.P) <= n * TOL
+    # five iterations: n * 1e-5, or three times the oracle's own response to a
+    # 1e-7 input perturbation where that is larger (ill-conditioned object edges)
+    tol = conditioned_tol(n * TOL, oracle_sensitivity(s, abc, n, probe_start=start))
+    assert rel_l2(xg, x) <= tol["x"]
+    assert rel_l2(O, prob.O) <= tol["O"]
+    assert rel_l2(P, prob.P) <= tol["P"]
     np.testing.assert_allclose(e, errs, rtol=n * TOL)
 
 

@@ -37,17 +37,25 @@ def _alone(scan, abc, n):
         return r.exit_waves(), O, P, r.errors()
 
 
-def test_batch_graph_equals_alone(scans):
+@pytest.mark.parametrize("mode", [serve.PTYCHO_BATCH_GROUPS, serve.PTYCHO_BATCH_BRANCHES,
+                                  serve.PTYCHO_BATCH_AUTO])
+def test_batch_graph_equals_alone(scans, mode):
     n = 6
     recons = []
     for sc in scans:
         r = native.Reconstruction()
         r.load_scan(sc.pos, sc.intensity, sc.obj0, sc.probe0)
         recons.append(r)
-    groups, ragged = serve.run_batch(recons, SETTINGS, n)
-    # every context is an FP32 cluster-design context: all of them run in the
-    # launch groups, one per pattern side (64, 128, 256)
-    assert (groups, ragged) == (3, len(scans))
+    info = serve.run_batch(recons, SETTINGS, n, mode=mode)
+    # every context is an FP32 cluster-design context: with launch groups, all
+    # of them run in the groups, one per pattern side (64, 128, 256)
+    if mode == serve.PTYCHO_BATCH_GROUPS:
+        assert (info["groups"], info["in_groups"], info["used"]) == (3, len(scans), "groups")
+    elif mode == serve.PTYCHO_BATCH_BRANCHES:
+        assert (info["groups"], info["used"]) == (0, "branches")
+    else:
+        assert info["groups_ms"] > 0 and info["branches_ms"] > 0
+        assert info["used"] == ("groups" if info["groups_ms"] <= info["branches_ms"] else "branches")
     for r, sc, abc in zip(recons, scans, SETTINGS):
         x, O, P, e = _alone(sc, abc, n)
         Ob, Pb = r.object_probe()
