@@ -511,12 +511,14 @@ def run_compare_mode(args):
 def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, e2e_iters: int,
                     local: int, ws: int, rank: int, concur: str = "deterministic",
                     fp32_compare: bool = False, divide: str = "auto", scan=None,
-                    with_e2e: bool = True):
+                    with_e2e: bool = True, shapes=None):
     """Time `steps` abc iterations of one scan on this rank's GPU (CUDA events on
     the library's stream, after `warmup` iterations), the dominant kernel's
     roofline, the clocks during the timed region, and one end-to-end
-    reconstruction through the C ABI from pinned host buffers.  Returns a dict
-    (the `scan` entry is the synthetic scan itself)."""
+    reconstruction through the C ABI from pinned host buffers.  `shapes`
+    (gather rows, gather columns, probe pixels per thread[, cluster size])
+    pins the launch shapes instead of tuning them.  Returns a dict (the `scan`
+    entry is the synthetic scan itself)."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -529,7 +531,11 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
     stream = torch.cuda.Stream(device=local)
     r = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=precision,
                               concur=concur, divide=divide)
+    if shapes:
+        r.set_tuning(False)
     r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+    if shapes:
+        r.set_launch_shapes(*shapes)
     design = r.divide_design()
     tuning = None
     abc = native.PRESETS[preset]
@@ -748,6 +754,10 @@ def main():
     ap.add_argument("--probe-start", type=int, default=10,
                     help="compare mode: the second reading holds the probe for this many iterations")
     ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--launch-shapes", default=None,
+                    type=lambda v: tuple(int(t) for t in v.split(",")),
+                    help="pin the launch shapes (gather rows,cols,probe pixels per thread[,cluster size]) "
+                         "instead of tuning them, e.g. for a profile of one kernel instance")
     args = ap.parse_args()
     if args.mode == "batch":
         return run_batch_mode(args)
@@ -778,7 +788,8 @@ def main():
 
     m = measure_iterate(spec, args.precision, args.preset, args.steps, args.warmup, args.e2e_iters,
                         local, ws, rank, concur=args.concur,
-                        fp32_compare=args.precision == "bf16x3", divide=args.divide)
+                        fp32_compare=args.precision == "bf16x3", divide=args.divide,
+                        shapes=args.launch_shapes)
     scan, value, ms, abc = m["scan"], m["value"], m["ms"], m["abc"]
     J, N = scan.J, scan.N
     NN = N * N

@@ -2,9 +2,15 @@
 // of the generalised divide-and-concur update on one GPU.
 //
 // Batch: the contexts' steady-state iteration (re-split prologue, divide,
-// concur) is captured once into a CUDA graph with one branch per context
-// (fork and join through events on a private stream) and replayed; the first
-// iteration, which may start from loaded exit waves, runs directly.
+// concur) is captured once into a CUDA graph and replayed; the first
+// iteration, which may start from loaded exit waves, runs directly.  Two
+// graph layouts: launch groups (the FP32 cluster-design contexts of one
+// pattern side run as one ragged divide launch over the (scan, wave) work
+// list of all their scans and one ragged launch per concur kernel; other
+// contexts keep a branch of their own), or one branch per context (fork and
+// join through events on a private stream).  In the automatic mode both
+// graphs are captured, one replay of each is timed, and the faster one is
+// replayed.  Every layout runs the same per-scan arithmetic.
 //
 // Server: FIFO admission under an HBM budget, a bounded active set, rounds of
 // a few iterations of every active request launched concurrently on the
