@@ -619,7 +619,7 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
         dist.barrier()
     w0 = time.perf_counter()
     re2e = native.Reconstruction(device=local, stream=stream.cuda_stream, precision=precision,
-                                 divide=divide)
+                                 concur=concur, divide=divide)
     re2e.load_scan(pos_h, I_h, O_h, P_h)
     re2e.iterate(*abc, e2e_iters)
     native.ptycho_get_object_probe(re2e.h, O_out, P_out)
@@ -828,8 +828,24 @@ def main():
                                 "divide_gbs": v["roofline"]["achieved"],
                                 "traffic": v["roofline"]["traffic"], "steps": 20, "warmup": 3,
                                 "clocks": v["clocks"]}
+    # the atomic concur mode (shared-memory-staged object atomics, register-
+    # staged probe atomics) against the deterministic gather, same scan
+    concur_modes = None
+    if (ws == 1 and not args.no_extras and args.precision == "fp32" and N == 256
+            and args.concur == "deterministic"):
+        a = measure_iterate(spec, "fp32", args.preset, 20, 3, 0, local, ws, rank,
+                            concur="atomic", scan=scan, with_e2e=False)
+        concur_modes = {
+            "deterministic": {"concur_ms": m["kernel_ms_per_step"]["concur"], "value": value},
+            "atomic": {"concur_ms": a["kernel_ms_per_step"]["concur"], "value": a["value"],
+                       "ms_per_step": a["ms"] / 20, "steps": 20, "warmup": 3,
+                       "clocks": a["clocks"]},
+            "note": "concur_ms: object + probe halves of the concur step per iteration (CUDA "
+                    "events); the atomic mode is not bitwise reproducible"}
     del scan, m["scan"]
     extra_launches = 2 * KERNELS_PER_ITER * 20 if variants is not None else 0
+    if concur_modes is not None:
+        extra_launches += (KERNELS_PER_ITER + 2) * 20
 
     # the rest of the metric (tensor-core path; serving) on a single GPU only
     extras = {}
@@ -877,7 +893,10 @@ def main():
                          "peak_source": "nominal (not measured)"},
             "per_step_bytes": (m["div_px"] + 16.0) * J * NN,
             "step_hbm_gbs": (m["div_px"] + 16.0) * J * NN / (ms / args.steps / 1e3) / 1e9,
-            "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)) * args.steps,
+            # the atomic concur mode adds two launches (the maxima of the
+            # atomically built denominators) and the tensor-core path four
+            "gpu_launches": (KERNELS_PER_ITER + (4 if args.precision == "bf16x3" else 0)
+                             + (2 if args.concur == "atomic" else 0)) * args.steps,
             "clocks": m["clocks"],
             "e2e": m["e2e"],
             "cpu_baseline": cpu,
@@ -886,6 +905,8 @@ def main():
             line["unfused_cufft"] = unfused
         if variants is not None:
             line["divide_variants"] = variants
+        if concur_modes is not None:
+            line["concur_modes"] = concur_modes
         if extra_launches:
             line["extra_timed_launches"] = extra_launches
         line.update(extras)

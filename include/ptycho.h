@@ -62,9 +62,16 @@ enum { PTYCHO_PREC_FP32 = 0,    /* FP32 shared-memory FFT (default) */
        PTYCHO_PREC_BF16X3 = 1   /* DFT as dense GEMMs on tensor cores, BF16 hi/lo
                                    split with three products, FP32 accumulation */ };
 
-/* How the concur step accumulates the object. */
-enum { PTYCHO_CONCUR_DETERMINISTIC = 0,  /* position-tiled gather, fixed order */
-       PTYCHO_CONCUR_ATOMIC = 1 };       /* per-position scatter with atomics */
+/* How the concur step (Fig. 3(b)) accumulates the object and probe numerators
+ * and denominators.  DETERMINISTIC: the object by a position-tiled gather and
+ * the probe by an ordered two-level reduction; bitwise reproducible.  ATOMIC:
+ * the object by shared-memory-staged atomics (groups of neighbouring
+ * positions accumulated band by band in a shared-memory box, then added to the
+ * global sums once per box pixel: FP32 numerator, FP64 denominator) and the
+ * probe by register-staged FP64 atomics; the same sums in an order that
+ * depends on timing, so not bitwise reproducible. */
+enum { PTYCHO_CONCUR_DETERMINISTIC = 0,
+       PTYCHO_CONCUR_ATOMIC = 1 };
 
 /* Kernel design of the FP32 divide step (Fig. 3(a)); both compute the same
  * update, within FP32 rounding of each other. */

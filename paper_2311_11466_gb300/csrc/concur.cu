@@ -16,6 +16,7 @@
 // in a fixed order: chunk order, or with many chunks contiguous groups of
 // chunks added in group order).  Maxima use integer atomicMax on the bit patterns of
 // non-negative IEEE values, which is order independent.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -225,6 +226,105 @@ __global__ void __launch_bounds__(kT) scatter_object_kernel(
     atomicAdd(denO + m, (double)cabs2(pv));
 }
 
+// Staged-atomic variant (the default of PTYCHO_CONCUR_ATOMIC): one CTA per
+// (group of positions, band of window rows).  The group's windows,
+// restricted to the band, lie in one box of the object (rows: the band's
+// rows plus the group's row spread; columns: N plus its column spread), which
+// is accumulated in shared memory and then added to the global numerator
+// (FP32 atomics) and denominator (FP64 atomics) once per box pixel instead
+// of once per window pixel.  Positions are added one after another with a
+// barrier between them, every thread taking the same window pixels of each
+// position, so no two threads touch a box pixel at once and the box needs no
+// shared-memory atomics; the band's probe values, the same for every
+// position of the group, are loaded once per thread.  The global atomics make
+// the order of the additions, and so the rounding, depend on timing: this
+// mode is not bitwise reproducible (the gather is).
+constexpr int kScatterCap = 8192;  // box pixels (float2 + float each: 96 KB of shared memory)
+constexpr int kScatterMaxG = 16;   // positions per group
+constexpr int kScatterPx = 8;      // window pixels per thread and band (a band is <= 2048 pixels)
+
+__global__ void __launch_bounds__(kT) scatter_staged_kernel(const ConcurScan cs) {
+    extern __shared__ float4 sc_smem[];
+    const int4 g = cs.cb.sc_groups[blockIdx.x];  // {first, count, row min, col min}
+    const int2 ex = cs.cb.sc_ext[blockIdx.x];    // {row spread, col spread}
+    const int N = cs.N, RB = cs.cb.sc_rows, band = blockIdx.y;
+    const int W = N + ex.y, HW = (RB + ex.x) * W;
+    const int r0 = g.z + band * RB;              // first object row of the box
+#if PT_DBG_ENABLED
+    // checked build: a box outside the object or the shared memory is recorded and skipped
+    if (r0 + RB + ex.x > cs.Mr || g.w + W > cs.Mc || HW > cs.cb.sc_box) {
+        if (threadIdx.x == 0) PT_DBG_FLAG(kDbgWindow);
+        return;
+    }
+#endif
+    float2* snum = reinterpret_cast<float2*>(sc_smem);
+    float* sden = reinterpret_cast<float*>(snum + HW);
+    for (int i = threadIdx.x; i < HW; i += kT) {
+        snum[i] = make_float2(0.f, 0.f);
+        sden[i] = 0.f;
+    }
+    const int lgN = __ffs(N) - 1;
+    const int band_px = RB * N;
+    const size_t NN = (size_t)N * N, band0 = (size_t)band * band_px;
+    float2 pv[kScatterPx];
+    float pd[kScatterPx];
+    int boff[kScatterPx];
+#pragma unroll
+    for (int i = 0; i < kScatterPx; ++i) {
+        const int p = threadIdx.x + i * kT;
+        const int rr = p >> lgN, cc = p & (N - 1);
+        pv[i] = p < band_px ? __ldg(cs.P + band0 + p) : make_float2(0.f, 0.f);
+        pd[i] = cabs2(pv[i]);
+        boff[i] = rr * W + cc;
+    }
+    const float2* __restrict__ y = cs.y;
+    float2 yv[kScatterPx];
+    int j = cs.cb.sc_ord[g.x];
+#pragma unroll
+    for (int i = 0; i < kScatterPx; ++i) {
+        const int p = threadIdx.x + i * kT;
+        yv[i] = p < band_px ? __ldcs(y + (size_t)j * NN + band0 + p) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();  // the box is zeroed
+    for (int k = 0; k < g.y; ++k) {
+        const int2 s = cs.pos[j];
+        const int base = (s.x - g.z) * W + (s.y - g.w);
+        // the next position's y, loaded before this one is added
+        float2 yn[kScatterPx];
+        const int jn = k + 1 < g.y ? cs.cb.sc_ord[g.x + k + 1] : j;
+#pragma unroll
+        for (int i = 0; i < kScatterPx; ++i) {
+            const int p = threadIdx.x + i * kT;
+            yn[i] = (k + 1 < g.y && p < band_px) ? __ldcs(y + (size_t)jn * NN + band0 + p)
+                                                : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kScatterPx; ++i) {
+            if (threadIdx.x + i * kT < band_px) {
+                const int b = base + boff[i];
+                snum[b] = cadd(snum[b], cconjmul(pv[i], yv[i]));
+                sden[b] += pd[i];
+            }
+        }
+        __syncthreads();
+        j = jn;
+#pragma unroll
+        for (int i = 0; i < kScatterPx; ++i) yv[i] = yn[i];
+    }
+    float2* __restrict__ numO = cs.cb.numO;
+    double* __restrict__ denO = cs.cb.denO;
+    for (int i = threadIdx.x; i < HW; i += kT) {
+        const float d = sden[i];
+        const float2 nv = snum[i];
+        if (d != 0.f || nv.x != 0.f || nv.y != 0.f) {
+            const int r = i / W, c = i - r * W;
+            const size_t m = (size_t)(r0 + r) * cs.Mc + g.w + c;
+            atomicAdd(numO + m, nv);
+            atomicAdd(denO + m, (double)d);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kT) max_double_kernel(const double* __restrict__ v, size_t n,
                                                         unsigned long long* __restrict__ out) {
     __shared__ double scratch[kT / 32];
@@ -256,8 +356,11 @@ __device__ __forceinline__ void onorm_body(const ConcurScan& cs, const int block
 // Probe partial sums over a chunk of positions; thread = PPT adjacent probe
 // pixels (PPT = 2: y read with 16-byte loads).  Each pixel adds its chunk's
 // positions in ascending order with the same operations for either PPT, so
-// both give bit-identical partials (a pure launch choice).
-template <int PPT>
+// both give bit-identical partials (a pure launch choice).  ATOMIC (the
+// atomic concur mode): the chunk's sums, staged in registers, are added to
+// the FP64 totals with FP64 atomics instead of being stored for the ordered
+// reduction.
+template <int PPT, bool ATOMIC = false>
 __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, const int ch) {
     static_assert(PPT == 1 || PPT == 2, "pixels per thread");
     const int N = cs.N, Mc = cs.Mc, J = cs.J, chunks = cs.cb.chunks;
@@ -304,8 +407,14 @@ __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, c
     }
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
-        cs.cb.partP[(size_t)ch * NN + r + i] = acc[i];
-        cs.cb.partPd[(size_t)ch * NN + r + i] = den[i];
+        if constexpr (ATOMIC) {
+            atomicAdd(&cs.cb.numP[r + i].x, (double)acc[i].x);
+            atomicAdd(&cs.cb.numP[r + i].y, (double)acc[i].y);
+            atomicAdd(cs.cb.denP + r + i, (double)den[i]);
+        } else {
+            cs.cb.partP[(size_t)ch * NN + r + i] = acc[i];
+            cs.cb.partPd[(size_t)ch * NN + r + i] = den[i];
+        }
     }
 }
 
@@ -414,6 +523,10 @@ __global__ void __launch_bounds__(kT) object_normalise_kernel(const ConcurScan c
 template <int PPT>
 __global__ void __launch_bounds__(kT) probe_partial_kernel(const ConcurScan cs) {
     ppart_body<PPT>(cs, blockIdx.x, blockIdx.y);
+}
+template <int PPT>
+__global__ void __launch_bounds__(kT) probe_partial_atomic_kernel(const ConcurScan cs) {
+    ppart_body<PPT, true>(cs, blockIdx.x, blockIdx.y);
 }
 template <int RG>
 __global__ void __launch_bounds__(kT) probe_reduce_kernel(const ConcurScan cs) {
@@ -560,6 +673,57 @@ void build_tile_csr(const int32_t* pos_rc, int J, int N, int Mr, int Mc, TileSha
     }
 }
 
+// Groups for the staged-atomic object concur.  A band of a window is at most
+// 2048 pixels (kScatterPx per thread); positions are taken in a spatial
+// order -- strips of rows N/16 high (at least 8), by column within a strip --
+// and a group grows while its box, band rows + row spread by N + column
+// spread, stays within kScatterCap pixels and it has at most kScatterMaxG
+// positions.  A raster row of a scan becomes a run of neighbours along the
+// columns, whose windows overlap the most.
+void build_scatter_groups(const int32_t* pos_rc, int J, int N, std::vector<int>& ord,
+                          std::vector<int4>& groups, std::vector<int2>& ext, int* rows, int* box) {
+    int rb = 2048 / N;
+    if (rb > N) rb = N;
+    if (rb < 1) rb = 1;
+    *rows = rb;
+    const int strip = N / 16 > 8 ? N / 16 : 8;
+    ord.resize((size_t)J);
+    for (int j = 0; j < J; ++j) ord[(size_t)j] = j;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const int sa = pos_rc[2 * a] / strip, sb = pos_rc[2 * b] / strip;
+        if (sa != sb) return sa < sb;
+        return pos_rc[2 * a + 1] < pos_rc[2 * b + 1];
+    });
+    groups.clear();
+    ext.clear();
+    int biggest = 0;
+    for (int k = 0; k < J;) {
+        const int j0 = ord[(size_t)k];
+        int rmin = pos_rc[2 * j0], rmax = rmin, cmin = pos_rc[2 * j0 + 1], cmax = cmin;
+        int cnt = 1;
+        while (k + cnt < J && cnt < kScatterMaxG) {
+            const int j = ord[(size_t)(k + cnt)];
+            const int r = pos_rc[2 * j], c = pos_rc[2 * j + 1];
+            const int nr0 = r < rmin ? r : rmin, nr1 = r > rmax ? r : rmax;
+            const int nc0 = c < cmin ? c : cmin, nc1 = c > cmax ? c : cmax;
+            if ((long)(rb + nr1 - nr0) * (N + nc1 - nc0) > kScatterCap) break;
+            rmin = nr0, rmax = nr1, cmin = nc0, cmax = nc1;
+            ++cnt;
+        }
+        groups.push_back(make_int4(k, cnt, rmin, cmin));
+        ext.push_back(make_int2(rmax - rmin, cmax - cmin));
+        const int b = (rb + rmax - rmin) * (N + cmax - cmin);
+        biggest = b > biggest ? b : biggest;
+        k += cnt;
+    }
+    *box = biggest;
+}
+
+cudaError_t concur_prepare() {
+    return cudaFuncSetAttribute(scatter_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kScatterCap * (sizeof(float2) + sizeof(float))));
+}
+
 size_t tile_csr_ptr_bound(int N, int Mr, int Mc) {
     (void)N;
     size_t m = 0;
@@ -625,8 +789,13 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
     } else {
         cudaMemsetAsync(cb.numO, 0, M * sizeof(float2), st);
         cudaMemsetAsync(cb.denO, 0, M * sizeof(double), st);
-        scatter_object_kernel<<<dim3((NN + kT - 1) / kT, cs.J), kT, 0, st>>>(cs.y, cs.P, cs.pos, cs.N,
-                                                                            cs.Mc, cb.numO, cb.denO);
+        if (cb.sc_n > 0) {
+            const size_t smem = (size_t)cb.sc_box * (sizeof(float2) + sizeof(float));
+            scatter_staged_kernel<<<dim3(cb.sc_n, cs.N / cb.sc_rows), kT, smem, st>>>(cs);
+        } else {
+            scatter_object_kernel<<<dim3((NN + kT - 1) / kT, cs.J), kT, 0, st>>>(
+                cs.y, cs.P, cs.pos, cs.N, cs.Mc, cb.numO, cb.denO);
+        }
         max_double_kernel<<<304, kT, 0, st>>>(cb.denO, M, cb.maxO);
     }
     object_normalise_kernel<<<(unsigned)((M + kT - 1) / kT), kT, 0, st>>>(cs);
@@ -642,11 +811,27 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         cudaMemsetAsync(cb.maxO, 0, sizeof(unsigned long long), st);
         return cudaGetLastError();
     }
+    const int n_slice = probe_reduce_blocks(cs.N, cb.chunks);
+    if (concur_mode != 0) {
+        // atomic mode: FP64 atomics of the register-staged chunk sums, then the
+        // probe maximum and the error slices (the probe maximum was cleared by
+        // the object normalisation)
+        cudaMemsetAsync(cb.numP, 0, NN * sizeof(double2), st);
+        cudaMemsetAsync(cb.denP, 0, NN * sizeof(double), st);
+        if (cb.probe_ppt == 2)
+            probe_partial_atomic_kernel<2><<<dim3((NN / 2 + kT - 1) / kT, cb.chunks), kT, 0, st>>>(cs);
+        else
+            probe_partial_atomic_kernel<1><<<dim3((NN + kT - 1) / kT, cb.chunks), kT, 0, st>>>(cs);
+        max_double_kernel<<<(NN + kT - 1) / kT < 304 ? (NN + kT - 1) / kT : 304, kT, 0, st>>>(
+            cb.denP, (size_t)NN, cb.maxP);
+        slice_sums_kernel<<<n_slice, kT, 0, st>>>(cs.e_part, cs.n_part, cb.e_slice);
+        probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cs, n_slice);
+        return cudaGetLastError();
+    }
     {
         cudaError_t e = launch_probe_partial(cs, st);
         if (e != cudaSuccess) return e;
     }
-    const int n_slice = probe_reduce_blocks(cs.N, cb.chunks);
     if (cb.chunks > kManyChunks)
         probe_reduce_kernel<8><<<n_slice, kT, 0, st>>>(cs);
     else

@@ -100,6 +100,15 @@ struct ConcurBufs {
     int tiles_r, tiles_c, chunks;
     int gather_shape;      // index into kGatherShape (a launch choice; same results)
     int probe_ppt;         // probe-partial pixels per thread, 1 or 2 (same results)
+    // staged-atomic object concur (PTYCHO_CONCUR_ATOMIC): positions in a
+    // spatial order, grouped so that a group's windows, band by band, fit a
+    // shared-memory box
+    int* sc_ord;           // [J] position indices, spatial order
+    int4* sc_groups;       // [sc_n] {first index into sc_ord, count, row min, col min}
+    int2* sc_ext;          // [sc_n] {row max - row min, col max - col min}
+    int sc_n;              // number of groups
+    int sc_rows;           // window rows per band (one CTA per group and band)
+    int sc_box;            // largest box of any group, pixels (shared memory: 12 B each)
 };
 
 // Object-gather tile shapes (rows x columns of the object) the tuner chooses
@@ -116,6 +125,12 @@ void build_tile_csr(const int32_t* pos_rc, int J, int N, int Mr, int Mc, TileSha
 // Upper bounds over every shape: tiles + 1 and CSR entries.
 size_t tile_csr_ptr_bound(int N, int Mr, int Mc);
 size_t tile_csr_entries_bound(int J, int N);
+// Host: position groups of the staged-atomic object concur (at most J groups).
+// Returns the window rows per band and the largest group box in pixels.
+void build_scatter_groups(const int32_t* pos_rc, int J, int N, std::vector<int>& ord,
+                          std::vector<int4>& groups, std::vector<int2>& ext, int* rows, int* box);
+// Shared-memory limit of the staged-atomic kernel on the current device.
+cudaError_t concur_prepare();
 // Everything the concur step of one scan needs on the device.
 struct ConcurScan {
     const float2* y;

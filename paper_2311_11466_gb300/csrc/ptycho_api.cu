@@ -398,6 +398,7 @@ size_t ptycho::scan_bytes(int J, int N, int M_rows, int M_cols, int precision, i
     b += (size_t)probe_reduce_blocks(N, (int)chunks) * sizeof(double);  // error slice totals
     b += tile_csr_ptr_bound(N, M_rows, M_cols) * sizeof(int) + tile_csr_entries_bound(J, N) * sizeof(int4);
     b += (size_t)J * ((NN + 255) / 256) * sizeof(double);  // load-time partial sums
+    b += (size_t)J * (sizeof(int) + sizeof(int4) + sizeof(int2));  // staged-atomic groups (bound)
     if (two) {
         const int ring = J < divide2p_ring() ? J : divide2p_ring();
         b += (size_t)ring * NN * sizeof(float2);                    // scratch ring
@@ -456,6 +457,13 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     std::vector<int4> tile_list;
     build_tile_csr(pos_rc, J, N, M_rows, M_cols, kGatherShape[tuned.gather_shape], tile_cnt, tile_list);
     const TileShape shape = kGatherShape[tuned.gather_shape];
+    // staged-atomic concur: position groups (integer work, done here)
+    const bool atomic = ctx->opts.concur == PTYCHO_CONCUR_ATOMIC;
+    std::vector<int> sc_ord;
+    std::vector<int4> sc_groups;
+    std::vector<int2> sc_ext;
+    int sc_rows = 0, sc_box = 0;
+    if (atomic) build_scatter_groups(pos_rc, J, N, sc_ord, sc_groups, sc_ext, &sc_rows, &sc_box);
     const int tiles_r = (M_rows + shape.rows - 1) / shape.rows;
     const int tiles_c = (M_cols + shape.cols - 1) / shape.cols;
 
@@ -466,6 +474,7 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     {
         cudaError_t pe = divide_prepare(N);
         if (pe == cudaSuccess && two) pe = divide2p_prepare();
+        if (pe == cudaSuccess && atomic) pe = concur_prepare();
         if (pe != cudaSuccess) return cuda_fail(ctx, pe, "divide_prepare");
     }
     const int sq_blocks = (int)((NN + 255) / 256);
@@ -510,6 +519,11 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     PT_ALLOC(ctx->cb.tile_ptr, tile_csr_ptr_bound(N, M_rows, M_cols));
     PT_ALLOC(ctx->cb.tile_win, tile_csr_entries_bound(J, N) > 0 ? tile_csr_entries_bound(J, N) : 1);
     PT_ALLOC(psum, (size_t)J * sq_blocks);
+    if (atomic) {
+        PT_ALLOC(ctx->cb.sc_ord, sc_ord.size());
+        PT_ALLOC(ctx->cb.sc_groups, sc_groups.size());
+        PT_ALLOC(ctx->cb.sc_ext, sc_ext.size());
+    }
     if (tc) {
         PT_ALLOC(ctx->sqrtI, (size_t)J * NN);
         for (int i = 0; i < 4; ++i) PT_ALLOC(ctx->planes[i], (size_t)J * NN * 2);
@@ -527,6 +541,9 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     ctx->cb.chunks = chunks;
     ctx->cb.gather_shape = tuned.gather_shape;
     ctx->cb.probe_ppt = tuned.probe_ppt;
+    ctx->cb.sc_n = (int)sc_groups.size();
+    ctx->cb.sc_rows = sc_rows;
+    ctx->cb.sc_box = sc_box;
     ctx->tuned = tuned.valid;
     ctx->pos_h.assign(pos_rc, pos_rc + 2 * (size_t)J);
     ctx->J = J;
@@ -561,6 +578,14 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     if (!tile_list.empty())
         PT_STEP(cudaMemcpyAsync(ctx->cb.tile_win, tile_list.data(), tile_list.size() * sizeof(int4),
                                 cudaMemcpyHostToDevice, st));
+    if (atomic) {
+        PT_STEP(cudaMemcpyAsync(ctx->cb.sc_ord, sc_ord.data(), sc_ord.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, st));
+        PT_STEP(cudaMemcpyAsync(ctx->cb.sc_groups, sc_groups.data(), sc_groups.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, st));
+        PT_STEP(cudaMemcpyAsync(ctx->cb.sc_ext, sc_ext.data(), sc_ext.size() * sizeof(int2),
+                                cudaMemcpyHostToDevice, st));
+    }
     PT_STEP(cudaMemsetAsync(ctx->dflag, 0, 4 * sizeof(int), st));
     PT_STEP(cudaMemsetAsync(ctx->d_iter, 0, sizeof(unsigned long long), st));
     PT_STEP(cudaMemsetAsync(ctx->cb.maxO, 0, sizeof(unsigned long long), st));
