@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (one context, FP32, 1024 exit waves of 256 x 256 on a 1300 x 1300
-object; the 4096-wave precision workload on the tensor-core path; and the
+object, with either concur mode; the 4096-wave precision workload on the tensor-core path; and the
 4096-wave 128 x 128 workload on the FP32 path).
 
 The FP64 oracle runs one whole RAAR iteration of the 1024-wave scan (about
@@ -31,19 +31,26 @@ def large():
     return synth.make_scan(synth.named_spec("large"))
 
 
-def test_large_raar_iteration_in_full(large):
-    abc = native.PRESETS["RAAR"]
+@pytest.fixture(scope="module")
+def large_ref(large):
+    """One FP64 RAAR iteration of the whole 1024-wave scan: x_1, O_1, P_1, E_F."""
     prob, x0 = oracle_problem(large)
-    x1 = prob.iterate(x0, *abc)
-    with gpu_recon(large) as r:
-        r.iterate(*abc, 1)
+    x1 = prob.iterate(x0, *native.PRESETS["RAAR"])
+    return x1, prob.O, prob.P, prob.last_error
+
+
+@pytest.mark.parametrize("concur", ["deterministic", "atomic"])
+def test_large_raar_iteration_in_full(large, large_ref, concur):
+    x1, O_ref, P_ref, e_ref = large_ref
+    with gpu_recon(large, concur=concur) as r:
+        r.iterate(*native.PRESETS["RAAR"], 1)
         O, P = r.object_probe()
         e = r.errors()
         x = r.exit_waves()
     assert rel_l2(x, x1) <= 1e-5
-    assert rel_l2(O, prob.O) <= 1e-5
-    assert rel_l2(P, prob.P) <= 1e-5
-    assert abs(e[0] - prob.last_error) <= 1e-5 * prob.last_error
+    assert rel_l2(O, O_ref) <= 1e-5
+    assert rel_l2(P, P_ref) <= 1e-5
+    assert abs(e[0] - e_ref) <= 1e-5 * e_ref
     # worst single exit wave, not only the aggregate
     worst = max(rel_l2(x[j], x1[j]) for j in range(0, large.J, 37))
     assert worst <= 1e-5
