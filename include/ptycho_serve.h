@@ -16,8 +16,8 @@
  * kernel over all their scans; other contexts have a branch of their own.
  *
  * Server: a request queue with admission by an HBM budget, continuous
- * batching (requests join the active set between rounds, as memory and slots
- * free up) and per-request latency.
+ * batching (requests join the active set as memory and slots free up, loaded
+ * while the other requests' iterations run) and per-request latency.
  *
  * Same conventions as ptycho.h: status codes, host buffers copied, outputs to
  * caller-allocated host buffers; a batch or server is not thread-safe.
@@ -98,11 +98,15 @@ int ptycho_server_create(ptycho_server** out, size_t hbm_budget_bytes, int32_t m
 int ptycho_server_submit(ptycho_server* srv, const ptycho_scan_desc* scan, float a, float b,
                          float c, int32_t n_iter, uint64_t* req_id);
 
-/* One scheduling round: admit queued requests in arrival order while they
- * fit, run up to iters_per_round iterations of every active request (all
- * concurrently), then retire finished requests (results copied to host,
- * device memory freed).  n_active / n_queued (either may be NULL) receive the
- * counts after the round.  Errors: EINVAL, ECUDA. */
+/* One scheduling step, which does not wait for the device to drain: retire
+ * requests whose iterations have all finished (results copied to host,
+ * device memory freed), admit queued requests in arrival order while they fit
+ * (their scans loaded while the other requests' work runs), and enqueue the
+ * next iters_per_round iterations of every active request whose previous
+ * round has finished, each on its own stream.  When none of these can be
+ * done it first waits (at most 2 s) for some round to finish.  Call it until
+ * n_active and n_queued are 0.  n_active / n_queued (either may be NULL)
+ * receive the counts after the step.  Errors: EINVAL, ECUDA. */
 int ptycho_server_step(ptycho_server* srv, int32_t iters_per_round, int32_t* n_active,
                        int32_t* n_queued);
 

@@ -108,7 +108,10 @@ int dalloc(ptycho_ctx* ctx, T** p, size_t count) {
     const size_t b = count * sizeof(T);
     if (b == 0) return PTYCHO_OK;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, b);
+    // stream-ordered allocation from the device's pool: freeing it later does
+    // not synchronise the device (cudaFree would), so a context that is
+    // destroyed does not stall the work of other contexts
+    cudaError_t e = cudaMallocAsync(&q, b, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PTYCHO_ENOMEM, "device allocation of " + std::to_string(b) +
@@ -121,7 +124,7 @@ int dalloc(ptycho_ctx* ctx, T** p, size_t count) {
 }
 
 void free_scan(ptycho_ctx* ctx) {
-    for (void* p : ctx->allocs) cudaFree(p);
+    for (void* p : ctx->allocs) cudaFreeAsync(p, ctx->stream);
     ctx->allocs.clear();
     ctx->bytes = 0;
     ctx->x = ctx->y = ctx->P = ctx->O = ctx->tw = nullptr;

@@ -13,10 +13,12 @@
 // replayed.  Every layout runs the same per-scan arithmetic.
 //
 // Server: FIFO admission under an HBM budget, a bounded active set, rounds of
-// a few iterations of every active request launched concurrently on the
-// requests' own streams, and retirement with result copy-back.  New requests
-// join between rounds (continuous batching); a finished request frees its
-// memory and slot for the next one in the queue.
+// a few iterations of every active request on the requests' own streams, and
+// retirement with result copy-back.  Rounds are not global: a request gets
+// its next round as soon as its previous one has finished, and new requests
+// are loaded while the others' rounds run (continuous batching); a finished
+// request frees its memory (stream-ordered, without synchronising the
+// device) and its slot for the next one in the queue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +29,7 @@
 #include <memory>
 #include <string>
 #include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "../../include/ptycho.h"
@@ -368,9 +371,11 @@ struct Request {
     std::vector<int32_t> pos;
     std::vector<float> inten, obj0, probe0;
     float a = 1, b = 1, c = 1;
-    int32_t n_iter = 0, done_iter = 0;
+    int32_t n_iter = 0, done_iter = 0;  // done_iter: iterations enqueued so far
     int32_t state = PTYCHO_REQ_QUEUED;
     ptycho_ctx* ctx = nullptr;
+    cudaEvent_t ev = nullptr;           // recorded after the last enqueued round
+    bool pending = false;               // that round may still be running
     size_t bytes = 0;
     Clock::time_point t_submit, t_admit, t_done;
     std::vector<float> obj_out, probe_out;
@@ -445,15 +450,37 @@ void retire(ptycho_server* s, Request* r) {
     r->probe_out.resize(2 * NN);
     int rc = ptycho_get_object_probe(r->ctx, r->obj_out.data(), r->probe_out.data());
     if (rc == PTYCHO_OK) rc = ptycho_model_error(r->ctx, &r->final_err);
-    ptycho_destroy(r->ctx);
+    ptycho_destroy(r->ctx);  // stream-ordered frees: the other requests keep running
     r->ctx = nullptr;
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->ev = nullptr;
     s->used -= r->bytes;
     r->t_done = Clock::now();
     r->state = rc == PTYCHO_OK ? PTYCHO_REQ_DONE : PTYCHO_REQ_FAILED;
 }
 
+// 1: the request's last enqueued round has finished (or none is pending);
+// 0: still running; < 0: a CUDA error.
+int round_done(Request* r) {
+    if (!r->pending) return 1;
+    const cudaError_t e = cudaEventQuery(r->ev);
+    if (e == cudaSuccess) {
+        r->pending = false;
+        return 1;
+    }
+    if (e == cudaErrorNotReady) return 0;
+    cudaGetLastError();
+    return -1;
+}
+
 }  // namespace
 
+// The step does not wait for a whole round of every request: it retires
+// requests whose work has finished, admits queued ones, and gives every
+// request whose previous round has finished its next round, so the device
+// keeps running the other requests' rounds while the host loads, admits and
+// retires.  When nothing could be done it waits (polling, at most 2 s) until
+// some round finishes, and tries once more.
 extern "C" int ptycho_server_step(ptycho_server* s, int32_t iters_per_round, int32_t* n_active,
                                   int32_t* n_queued) {
     NvtxRange nvtx_range("ptycho_server_step");
@@ -466,58 +493,83 @@ extern "C" int ptycho_server_step(ptycho_server* s, int32_t iters_per_round, int
         ~Restore() { cudaSetDevice(d); }
     } restore{prev};
 
-    // admission, in arrival order
-    while (!s->queue.empty() && (int32_t)s->active.size() < s->max_active) {
-        Request* r = s->queue.front();
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return PTYCHO_ECUDA;
-        const size_t margin = (size_t)1 << 30;
-        if (s->used + r->bytes > s->budget || r->bytes + margin > free_b) break;
-        s->queue.pop_front();
-        ptycho_ctx* ctx = nullptr;
-        int rc = ptycho_create(&ctx, &s->opts);
-        if (rc == PTYCHO_OK)
-            rc = ptycho_load_scan(ctx, r->J, r->N, r->pos.data(), r->inten.data(), r->Mr, r->Mc,
-                                  r->obj0.data(), r->probe0.data(), 0);
-        if (rc != PTYCHO_OK) {
-            if (ctx) ptycho_destroy(ctx);
-            r->state = PTYCHO_REQ_FAILED;
-            r->t_done = Clock::now();
-            continue;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        bool progressed = false;
+        // retirement: every iteration enqueued and the last round finished
+        std::vector<Request*> still;
+        for (Request* r : s->active) {
+            const int d = round_done(r);
+            if (d < 0) return PTYCHO_ECUDA;
+            if (d == 1 && r->done_iter >= r->n_iter) {
+                retire(s, r);
+                progressed = true;
+            } else {
+                still.push_back(r);
+            }
         }
-        r->ctx = ctx;
-        r->state = PTYCHO_REQ_ACTIVE;
-        r->t_admit = Clock::now();
-        s->used += r->bytes;
-        // the scan now lives on the device
-        std::vector<float>().swap(r->inten);
-        std::vector<float>().swap(r->obj0);
-        std::vector<int32_t>().swap(r->pos);
-        std::vector<float>().swap(r->probe0);
-        s->active.push_back(r);
-    }
+        s->active.swap(still);
 
-    // one round: every active request advances concurrently on its own stream
-    for (Request* r : s->active) {
-        const int32_t k = std::min(iters_per_round, r->n_iter - r->done_iter);
-        if (k > 0) {
-            int rc = ptycho_iterate(r->ctx, r->a, r->b, r->c, k);
-            if (rc != PTYCHO_OK) return rc;
-            r->done_iter += k;
+        // admission, in arrival order
+        while (!s->queue.empty() && (int32_t)s->active.size() < s->max_active) {
+            Request* r = s->queue.front();
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return PTYCHO_ECUDA;
+            const size_t margin = (size_t)1 << 30;
+            if (s->used + r->bytes > s->budget || r->bytes + margin > free_b) break;
+            s->queue.pop_front();
+            progressed = true;
+            ptycho_ctx* ctx = nullptr;
+            int rc = ptycho_create(&ctx, &s->opts);
+            if (rc == PTYCHO_OK)
+                rc = ptycho_load_scan(ctx, r->J, r->N, r->pos.data(), r->inten.data(), r->Mr, r->Mc,
+                                      r->obj0.data(), r->probe0.data(), 0);
+            if (rc == PTYCHO_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+                rc = PTYCHO_ECUDA;
+            if (rc != PTYCHO_OK) {
+                if (ctx) ptycho_destroy(ctx);
+                r->ev = nullptr;
+                r->state = PTYCHO_REQ_FAILED;
+                r->t_done = Clock::now();
+                continue;
+            }
+            r->ctx = ctx;
+            r->state = PTYCHO_REQ_ACTIVE;
+            r->t_admit = Clock::now();
+            s->used += r->bytes;
+            // the scan now lives on the device
+            std::vector<float>().swap(r->inten);
+            std::vector<float>().swap(r->obj0);
+            std::vector<int32_t>().swap(r->pos);
+            std::vector<float>().swap(r->probe0);
+            s->active.push_back(r);
+        }
+
+        // rounds: the next iterations of every request whose previous round finished
+        for (Request* r : s->active) {
+            const int d = round_done(r);
+            if (d < 0) return PTYCHO_ECUDA;
+            const int32_t k = std::min(iters_per_round, r->n_iter - r->done_iter);
+            if (d == 1 && k > 0) {
+                int rc = ptycho_iterate(r->ctx, r->a, r->b, r->c, k);
+                if (rc != PTYCHO_OK) return rc;
+                r->done_iter += k;
+                if (cudaEventRecord(r->ev, ptycho::ctx_stream(r->ctx)) != cudaSuccess) return PTYCHO_ECUDA;
+                r->pending = true;
+                progressed = true;
+            }
+        }
+        if (progressed || s->active.empty() || attempt == 1) break;
+        // nothing to do until a round finishes
+        const auto t0 = Clock::now();
+        for (bool any = false; !any && seconds(t0, Clock::now()) < 2.0;) {
+            for (Request* r : s->active) {
+                const int d = round_done(r);
+                if (d < 0) return PTYCHO_ECUDA;
+                any = any || d == 1;
+            }
+            if (!any) std::this_thread::sleep_for(std::chrono::microseconds(50));
         }
     }
-    for (Request* r : s->active)
-        if (cudaStreamSynchronize(ptycho::ctx_stream(r->ctx)) != cudaSuccess) return PTYCHO_ECUDA;
-
-    // retirement
-    std::vector<Request*> still;
-    for (Request* r : s->active) {
-        if (r->done_iter >= r->n_iter)
-            retire(s, r);
-        else
-            still.push_back(r);
-    }
-    s->active.swap(still);
     if (n_active) *n_active = (int32_t)s->active.size();
     if (n_queued) *n_queued = (int32_t)s->queue.size();
     return PTYCHO_OK;
@@ -545,7 +597,9 @@ extern "C" int ptycho_server_poll(ptycho_server* s, uint64_t id, int32_t* state,
 
 extern "C" void ptycho_server_destroy(ptycho_server* s) {
     if (!s) return;
-    for (Request* r : s->active)
+    for (Request* r : s->active) {
         if (r->ctx) ptycho_destroy(r->ctx);
+        if (r->ev) cudaEventDestroy(r->ev);
+    }
     delete s;
 }

@@ -188,6 +188,11 @@ def run_stream(scans, settings, n_iter: int, arrivals_s, budget_bytes: int, max_
                                               *settings[i], n_iter)
                 nxt += 1
             na, nq = ptycho_server_step(s, iters_per_round)
+            if nxt - na - nq == len(done):   # nxt requests submitted so far
+                # no request finished in this step: nothing to poll
+                if na == 0 and nq == 0 and nxt < len(order):
+                    time.sleep(max(0.0, min(0.01, arrivals_s[order[nxt]] - (time.perf_counter() - t0))))
+                continue
             for i, rid in enumerate(ids):
                 if rid is None or i in done:
                     continue
