@@ -241,25 +241,34 @@ __global__ void __launch_bounds__(kT) scatter_object_kernel(
 // mode is not bitwise reproducible (the gather is).
 constexpr int kScatterCap = 8192;  // box pixels (float2 + float each: 96 KB of shared memory)
 constexpr int kScatterMaxG = 16;   // positions per group
-constexpr int kScatterPx = 8;      // window pixels per thread and band (a band is <= 2048 pixels)
+constexpr int kScT = 512;          // threads of the staged kernel (two CTAs per SM)
+constexpr int kScatterPx = 4;      // window pixels per thread and band (a band is <= 2048 pixels)
 
-__global__ void __launch_bounds__(kT) scatter_staged_kernel(const ConcurScan cs) {
+__global__ void __launch_bounds__(kScT, 2) scatter_staged_kernel(const ConcurScan cs) {
     extern __shared__ float4 sc_smem[];
+    __shared__ int s_j[kScatterMaxG], s_base[kScatterMaxG];
     const int4 g = cs.cb.sc_groups[blockIdx.x];  // {first, count, row min, col min}
     const int2 ex = cs.cb.sc_ext[blockIdx.x];    // {row spread, col spread}
     const int N = cs.N, RB = cs.cb.sc_rows, band = blockIdx.y;
-    const int W = N + ex.y, HW = (RB + ex.x) * W;
+    const int H = RB + ex.x, W = N + ex.y, HW = H * W;
     const int r0 = g.z + band * RB;              // first object row of the box
 #if PT_DBG_ENABLED
     // checked build: a box outside the object or the shared memory is recorded and skipped
-    if (r0 + RB + ex.x > cs.Mr || g.w + W > cs.Mc || HW > cs.cb.sc_box) {
+    if (r0 + H > cs.Mr || g.w + W > cs.Mc || HW > cs.cb.sc_box || g.y > kScatterMaxG) {
         if (threadIdx.x == 0) PT_DBG_FLAG(kDbgWindow);
         return;
     }
 #endif
     float2* snum = reinterpret_cast<float2*>(sc_smem);
     float* sden = reinterpret_cast<float*>(snum + HW);
-    for (int i = threadIdx.x; i < HW; i += kT) {
+    // the group's positions and their offsets in the box
+    if ((int)threadIdx.x < g.y) {
+        const int j = cs.cb.sc_ord[g.x + threadIdx.x];
+        const int2 s = cs.pos[j];
+        s_j[threadIdx.x] = j;
+        s_base[threadIdx.x] = (s.x - g.z) * W + (s.y - g.w);
+    }
+    for (int i = threadIdx.x; i < HW; i += kScT) {
         snum[i] = make_float2(0.f, 0.f);
         sden[i] = 0.f;
     }
@@ -271,49 +280,50 @@ __global__ void __launch_bounds__(kT) scatter_staged_kernel(const ConcurScan cs)
     int boff[kScatterPx];
 #pragma unroll
     for (int i = 0; i < kScatterPx; ++i) {
-        const int p = threadIdx.x + i * kT;
+        const int p = threadIdx.x + i * kScT;
         const int rr = p >> lgN, cc = p & (N - 1);
         pv[i] = p < band_px ? __ldg(cs.P + band0 + p) : make_float2(0.f, 0.f);
         pd[i] = cabs2(pv[i]);
         boff[i] = rr * W + cc;
     }
+    __syncthreads();  // the box is zeroed, the position table written
     const float2* __restrict__ y = cs.y;
     float2 yv[kScatterPx];
-    int j = cs.cb.sc_ord[g.x];
+    {
+        const int j0 = s_j[0];
 #pragma unroll
-    for (int i = 0; i < kScatterPx; ++i) {
-        const int p = threadIdx.x + i * kT;
-        yv[i] = p < band_px ? __ldcs(y + (size_t)j * NN + band0 + p) : make_float2(0.f, 0.f);
+        for (int i = 0; i < kScatterPx; ++i) {
+            const int p = threadIdx.x + i * kScT;
+            yv[i] = p < band_px ? __ldcs(y + (size_t)j0 * NN + band0 + p) : make_float2(0.f, 0.f);
+        }
     }
-    __syncthreads();  // the box is zeroed
     for (int k = 0; k < g.y; ++k) {
-        const int2 s = cs.pos[j];
-        const int base = (s.x - g.z) * W + (s.y - g.w);
         // the next position's y, loaded before this one is added
         float2 yn[kScatterPx];
-        const int jn = k + 1 < g.y ? cs.cb.sc_ord[g.x + k + 1] : j;
+        const bool more = k + 1 < g.y;
+        const int jn = more ? s_j[k + 1] : 0;
 #pragma unroll
         for (int i = 0; i < kScatterPx; ++i) {
-            const int p = threadIdx.x + i * kT;
-            yn[i] = (k + 1 < g.y && p < band_px) ? __ldcs(y + (size_t)jn * NN + band0 + p)
-                                                : make_float2(0.f, 0.f);
+            const int p = threadIdx.x + i * kScT;
+            yn[i] = (more && p < band_px) ? __ldcs(y + (size_t)jn * NN + band0 + p)
+                                          : make_float2(0.f, 0.f);
         }
+        const int base = s_base[k];
 #pragma unroll
         for (int i = 0; i < kScatterPx; ++i) {
-            if (threadIdx.x + i * kT < band_px) {
+            if (threadIdx.x + i * kScT < band_px) {
                 const int b = base + boff[i];
                 snum[b] = cadd(snum[b], cconjmul(pv[i], yv[i]));
                 sden[b] += pd[i];
             }
         }
         __syncthreads();
-        j = jn;
 #pragma unroll
         for (int i = 0; i < kScatterPx; ++i) yv[i] = yn[i];
     }
     float2* __restrict__ numO = cs.cb.numO;
     double* __restrict__ denO = cs.cb.denO;
-    for (int i = threadIdx.x; i < HW; i += kT) {
+    for (int i = threadIdx.x; i < HW; i += kScT) {
         const float d = sden[i];
         const float2 nv = snum[i];
         if (d != 0.f || nv.x != 0.f || nv.y != 0.f) {
@@ -791,7 +801,7 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         cudaMemsetAsync(cb.denO, 0, M * sizeof(double), st);
         if (cb.sc_n > 0) {
             const size_t smem = (size_t)cb.sc_box * (sizeof(float2) + sizeof(float));
-            scatter_staged_kernel<<<dim3(cb.sc_n, cs.N / cb.sc_rows), kT, smem, st>>>(cs);
+            scatter_staged_kernel<<<dim3(cb.sc_n, cs.N / cb.sc_rows), kScT, smem, st>>>(cs);
         } else {
             scatter_object_kernel<<<dim3((NN + kT - 1) / kT, cs.J), kT, 0, st>>>(
                 cs.y, cs.P, cs.pos, cs.N, cs.Mc, cb.numO, cb.denO);
