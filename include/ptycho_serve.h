@@ -101,7 +101,9 @@ int ptycho_server_submit(ptycho_server* srv, const ptycho_scan_desc* scan, float
 /* One scheduling step, which does not wait for the device to drain: retire
  * requests whose iterations have all finished (results copied to host,
  * device memory freed), admit queued requests in arrival order while they fit
- * (their scans loaded while the other requests' work runs), and enqueue the
+ * (their scans loaded while the other requests' work runs; a request that
+ * does not fit the device's free memory while nothing else is active fails,
+ * state PTYCHO_REQ_FAILED), and enqueue the
  * next iters_per_round iterations of every active request whose previous
  * round has finished, each on its own stream.  When none of these can be
  * done it first waits (at most 2 s) for some round to finish.  Call it until

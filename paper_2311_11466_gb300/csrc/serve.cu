@@ -512,10 +512,27 @@ extern "C" int ptycho_server_step(ptycho_server* s, int32_t iters_per_round, int
         // admission, in arrival order
         while (!s->queue.empty() && (int32_t)s->active.size() < s->max_active) {
             Request* r = s->queue.front();
+            if (s->used + r->bytes > s->budget) break;
             size_t free_b = 0, total_b = 0;
             if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return PTYCHO_ECUDA;
             const size_t margin = (size_t)1 << 30;
-            if (s->used + r->bytes > s->budget || r->bytes + margin > free_b) break;
+            if (r->bytes + margin > free_b) {
+                // memory freed by retired requests may still sit in the
+                // stream-ordered pool: hand it back to the device, then look again
+                cudaMemPool_t pool;
+                if (cudaDeviceGetDefaultMemPool(&pool, s->opts.device) == cudaSuccess)
+                    cudaMemPoolTrimTo(pool, 0);
+                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return PTYCHO_ECUDA;
+                if (r->bytes + margin > free_b) {
+                    if (!s->active.empty()) break;  // wait for a request to retire
+                    // nothing runs that could free memory: it can never fit
+                    s->queue.pop_front();
+                    r->state = PTYCHO_REQ_FAILED;
+                    r->t_done = Clock::now();
+                    progressed = true;
+                    continue;
+                }
+            }
             s->queue.pop_front();
             progressed = true;
             ptycho_ctx* ctx = nullptr;
