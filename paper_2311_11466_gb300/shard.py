@@ -26,7 +26,7 @@ windows cover a compact band of the object), and:
 The maxima are taken after the sums (the maximum of per-rank maxima would be
 a different regulariser).  The per-iteration Fourier error is a sum of
 per-rank partial sums (one more scalar all-reduce).  Plain point-to-point
-loads over the interconnect suffice; no multicast is needed.
+loads over the interconnect (NCCL's own algorithms) suffice.
 
 A halo exchange of only the overlapping band of the object would move less
 than step 2 when the ranks' bands are thin, at the price of a position-
