@@ -109,8 +109,10 @@ __device__ __forceinline__ void gather_body(const ConcurScan& cs, const int tile
     // P are in flight at once (a window that misses a pixel loads P[0] and no y).
     auto add_one = [&](const int4 w, const int k, float2 pv, float2 yv) {
         (void)w;
-        acc[k] = cadd(acc[k], cconjmul(pv, yv));
-        dg[k] += cabs2(pv);
+        // conj(P) y and |P|^2 as chains of fused multiply-adds into the sums
+        acc[k].x = fmaf(pv.x, yv.x, fmaf(pv.y, yv.y, acc[k].x));
+        acc[k].y = fmaf(pv.x, yv.y, fmaf(-pv.y, yv.x, acc[k].y));
+        dg[k] = fmaf(pv.x, pv.x, fmaf(pv.y, pv.y, dg[k]));
     };
     auto add_range = [&](const int4* ent, int n) {
         constexpr int kGroup = 4;
@@ -411,8 +413,10 @@ __device__ __forceinline__ void ppart_body(const ConcurScan& cs, const int bx, c
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
             const float2 ov = __ldg(op + i);
-            acc[i] = cadd(acc[i], cconjmul(ov, yv[i]));
-            den[i] += cabs2(ov);
+            // conj(O) y and |O|^2 as chains of fused multiply-adds into the sums
+            acc[i].x = fmaf(ov.x, yv[i].x, fmaf(ov.y, yv[i].y, acc[i].x));
+            acc[i].y = fmaf(ov.x, yv[i].y, fmaf(-ov.y, yv[i].x, acc[i].y));
+            den[i] = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, den[i]));
         }
     }
 #pragma unroll
