@@ -315,7 +315,10 @@ __global__ void __launch_bounds__(kScT, 2) scatter_staged_kernel(const ConcurSca
         for (int i = 0; i < kScatterPx; ++i) {
             if (threadIdx.x + i * kScT < band_px) {
                 const int b = base + boff[i];
-                snum[b] = cadd(snum[b], cconjmul(pv[i], yv[i]));
+                float2 sv = snum[b];
+                sv.x = fmaf(pv[i].x, yv[i].x, fmaf(pv[i].y, yv[i].y, sv.x));
+                sv.y = fmaf(pv[i].x, yv[i].y, fmaf(-pv[i].y, yv[i].x, sv.y));
+                snum[b] = sv;
                 sden[b] += pd[i];
             }
         }
