@@ -115,7 +115,7 @@ __device__ __forceinline__ void gather_body(const ConcurScan& cs, const int tile
         dg[k] = fmaf(pv.x, pv.x, fmaf(pv.y, pv.y, dg[k]));
     };
     auto add_range = [&](const int4* ent, int n) {
-        constexpr int kGroup = 4;
+        constexpr int kGroup = 8;
         int l = 0;
         for (; l + kGroup <= n; l += kGroup) {
             float2 pv[kGroup][KP], yv[kGroup][KP];
