@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ptycho.h"
@@ -121,6 +122,27 @@ int dalloc(ptycho_ctx* ctx, T** p, size_t count) {
     ctx->bytes += b;
     *p = static_cast<T*>(q);
     return PTYCHO_OK;
+}
+
+// The device's stream-ordered pool (context memory) keeps what contexts free
+// instead of handing it back to the driver at the next synchronisation, so a
+// context that follows another (a served request, a reconstruction after a
+// reconstruction) reuses the mapped memory.  A process-local setting of this
+// process's pool; the server trims the pool before it refuses a request for
+// lack of free device memory.
+void keep_pool_memory(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int d : done)
+        if (d == device) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(device);
 }
 
 void free_scan(ptycho_ctx* ctx) {
@@ -335,6 +357,7 @@ int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts) {
         return e != cudaSuccess ? PTYCHO_ECUDA : PTYCHO_EINVAL;
     }
     DeviceGuard dg(o.device);
+    keep_pool_memory(o.device);
     ptycho_ctx* ctx = new ptycho_ctx();
     ctx->opts = o;
     if (o.stream) {
