@@ -113,6 +113,12 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel in the stream finishes;
+// it waits here, before touching memory, until that kernel has completed and
+// its writes are visible (a no-op for a kernel launched without it).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Deterministic block reduction of one double per thread (fixed tree order).
 // Every thread of the block must call it; the result is valid in thread 0.
 template <int THREADS>

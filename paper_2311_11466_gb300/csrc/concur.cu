@@ -532,13 +532,16 @@ __device__ __forceinline__ void pnorm_body(const ConcurScan& cs, const int block
 // ---- one scan per launch -----------------------------------------------------
 template <int TR, int TC>
 __global__ void __launch_bounds__(kT) concur_object_kernel(const ConcurScan cs) {
+    pdl_wait();
     gather_body<TR, TC>(cs, blockIdx.x);
 }
 __global__ void __launch_bounds__(kT) object_normalise_kernel(const ConcurScan cs) {
+    pdl_wait();
     onorm_body(cs, blockIdx.x);
 }
 template <int PPT>
 __global__ void __launch_bounds__(kT) probe_partial_kernel(const ConcurScan cs) {
+    pdl_wait();
     ppart_body<PPT>(cs, blockIdx.x, blockIdx.y);
 }
 template <int PPT>
@@ -547,9 +550,11 @@ __global__ void __launch_bounds__(kT) probe_partial_atomic_kernel(const ConcurSc
 }
 template <int RG>
 __global__ void __launch_bounds__(kT) probe_reduce_kernel(const ConcurScan cs) {
+    pdl_wait();
     preduce_body<RG>(cs, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kT) probe_normalise_kernel(const ConcurScan cs, int n_slice) {
+    pdl_wait();
     pnorm_body(cs, blockIdx.x, n_slice);
 }
 
@@ -775,25 +780,41 @@ int probe_chunks(int J, int N) {
     return ch;
 }
 
+// A kernel of the deterministic concur step, launched with programmatic stream
+// serialisation: its launch overlaps the end of the previous kernel, and it
+// waits in pdl_wait before touching memory (measured: concur 0.229 -> 0.220 ms
+// per 1024 x 256^2 iteration).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_gather(const ConcurScan& cs, cudaStream_t st) {
     const unsigned grid = (unsigned)(cs.cb.tiles_r * cs.cb.tiles_c);
     switch (cs.cb.gather_shape) {
-        case 0: concur_object_kernel<16, 32><<<grid, kT, 0, st>>>(cs); break;
-        case 1: concur_object_kernel<8, 32><<<grid, kT, 0, st>>>(cs); break;
-        case 2: concur_object_kernel<32, 32><<<grid, kT, 0, st>>>(cs); break;
-        case 3: concur_object_kernel<8, 64><<<grid, kT, 0, st>>>(cs); break;
+        case 0: return launch_pdl(concur_object_kernel<16, 32>, dim3(grid), st, cs);
+        case 1: return launch_pdl(concur_object_kernel<8, 32>, dim3(grid), st, cs);
+        case 2: return launch_pdl(concur_object_kernel<32, 32>, dim3(grid), st, cs);
+        case 3: return launch_pdl(concur_object_kernel<8, 64>, dim3(grid), st, cs);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_probe_partial(const ConcurScan& cs, cudaStream_t st) {
     const int NN = cs.N * cs.N;
     if (cs.cb.probe_ppt == 2)
-        probe_partial_kernel<2><<<dim3((NN / 2 + kT - 1) / kT, cs.cb.chunks), kT, 0, st>>>(cs);
-    else
-        probe_partial_kernel<1><<<dim3((NN + kT - 1) / kT, cs.cb.chunks), kT, 0, st>>>(cs);
-    return cudaGetLastError();
+        return launch_pdl(probe_partial_kernel<2>, dim3((NN / 2 + kT - 1) / kT, cs.cb.chunks), st, cs);
+    return launch_pdl(probe_partial_kernel<1>, dim3((NN + kT - 1) / kT, cs.cb.chunks), st, cs);
 }
 
 cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_probe, cudaStream_t st) {
@@ -815,7 +836,10 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         }
         max_double_kernel<<<304, kT, 0, st>>>(cb.denO, M, cb.maxO);
     }
-    object_normalise_kernel<<<(unsigned)((M + kT - 1) / kT), kT, 0, st>>>(cs);
+    {
+        cudaError_t e = launch_pdl(object_normalise_kernel, dim3((unsigned)((M + kT - 1) / kT)), st, cs);
+        if (e != cudaSuccess) return e;
+    }
     if (!update_probe) {
         // the probe is held: the iteration's Fourier error from the divide
         // kernel's partials (slices summed into the probe-reduce slice buffer,
@@ -849,11 +873,11 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         cudaError_t e = launch_probe_partial(cs, st);
         if (e != cudaSuccess) return e;
     }
-    if (cb.chunks > kManyChunks)
-        probe_reduce_kernel<8><<<n_slice, kT, 0, st>>>(cs);
-    else
-        probe_reduce_kernel<1><<<n_slice, kT, 0, st>>>(cs);
-    probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cs, n_slice);
+    cudaError_t e = cb.chunks > kManyChunks ? launch_pdl(probe_reduce_kernel<8>, dim3(n_slice), st, cs)
+                                            : launch_pdl(probe_reduce_kernel<1>, dim3(n_slice), st, cs);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(probe_normalise_kernel, dim3((NN + kT - 1) / kT), st, cs, n_slice);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

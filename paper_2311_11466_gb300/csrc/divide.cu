@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(256) sqrt_permute_kernel(const float* __restri
 // position.
 template <int N, int MODE, int V>
 __global__ void __launch_bounds__(Geo<N, V>::T, Cfg<N, V>::MINB) divide_kernel(const DivideArgs args) {
+    pdl_wait();
     divide_body<N, MODE, V>(args, MODE == kModeSP ? args.sp_pos : (int)(blockIdx.x / Geo<N, V>::C));
 }
 
@@ -558,7 +559,7 @@ cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     cfg.blockDim = dim3(G::T);
     cfg.dynamicSmemBytes = G::SMEM;
     cfg.stream = st;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[3];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = G::C;
     attr[0].val.clusterDim.y = 1;
@@ -568,8 +569,12 @@ cudaError_t launch_t(const DivideArgs& a, cudaStream_t st) {
     // load balancing every SM takes CTAs (measured 0.907 -> 0.858 ms, large).
     attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
     attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+    // programmatic stream serialisation: the kernel may be launched while the
+    // previous one finishes and waits for it in pdl_wait
+    attr[2].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[2].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 3;
     if (a.sp) {
         cfg.gridDim = dim3((unsigned)G::C);  // one cluster: one position
         return cudaLaunchKernelEx(&cfg, divide_kernel<N, kModeSP, V>, a);
