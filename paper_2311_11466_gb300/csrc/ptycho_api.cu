@@ -566,7 +566,9 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     ctx->cb.tiles_c = tiles_c;
     ctx->cb.chunks = chunks;
     ctx->cb.gather_shape = tuned.gather_shape;
-    ctx->cb.probe_ppt = tuned.probe_ppt;
+    // the tuner times the deterministic probe pass; the atomic one, with more
+    // registers, keeps one pixel per thread unless pinned
+    ctx->cb.probe_ppt = atomic ? 1 : tuned.probe_ppt;
     ctx->cb.sc_n = (int)sc_groups.size();
     ctx->cb.sc_rows = sc_rows;
     ctx->cb.sc_box = sc_box;
