@@ -247,6 +247,7 @@ constexpr int kScT = 512;          // threads of the staged kernel (two CTAs per
 constexpr int kScatterPx = 4;      // window pixels per thread and band (a band is <= 2048 pixels)
 
 __global__ void __launch_bounds__(kScT, 2) scatter_staged_kernel(const ConcurScan cs) {
+    pdl_wait();
     extern __shared__ float4 sc_smem[];
     __shared__ int s_j[kScatterMaxG], s_base[kScatterMaxG];
     const int4 g = cs.cb.sc_groups[blockIdx.x];  // {first, count, row min, col min}
@@ -342,6 +343,7 @@ __global__ void __launch_bounds__(kScT, 2) scatter_staged_kernel(const ConcurSca
 
 __global__ void __launch_bounds__(kT) max_double_kernel(const double* __restrict__ v, size_t n,
                                                         unsigned long long* __restrict__ out) {
+    pdl_wait();
     __shared__ double scratch[kT / 32];
     double m = 0.0;
     for (size_t i = blockIdx.x * (size_t)kT + threadIdx.x; i < n; i += (size_t)gridDim.x * kT)
@@ -546,6 +548,7 @@ __global__ void __launch_bounds__(kT) probe_partial_kernel(const ConcurScan cs) 
 }
 template <int PPT>
 __global__ void __launch_bounds__(kT) probe_partial_atomic_kernel(const ConcurScan cs) {
+    pdl_wait();
     ppart_body<PPT, true>(cs, blockIdx.x, blockIdx.y);
 }
 template <int RG>
@@ -607,6 +610,7 @@ __global__ void __launch_bounds__(kT) ragged_pnorm_kernel(const ConcurScan* __re
 // Stage 1 of a two-level sum: block b adds the contiguous slice b of parts.
 __global__ void __launch_bounds__(kT) slice_sums_kernel(const double* __restrict__ parts, int n,
                                                         double* __restrict__ out) {
+    pdl_wait();
     __shared__ double scratch[kT / 32];
     const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
     const int e0 = (int)blockIdx.x * per, e1 = min(n, e0 + per);
@@ -785,11 +789,12 @@ int probe_chunks(int J, int N) {
 // waits in pdl_wait before touching memory (measured: concur 0.229 -> 0.220 ms
 // per 1024 x 256^2 iteration).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, cudaStream_t st, Args... args) {
+cudaError_t launch_pdl_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(kT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -797,6 +802,10 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, cudaStream_t st, Args.
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, cudaStream_t st, Args... args) {
+    return launch_pdl_ex(kern, grid, dim3(kT), 0, st, args...);
 }
 
 cudaError_t launch_gather(const ConcurScan& cs, cudaStream_t st) {
@@ -829,12 +838,15 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         cudaMemsetAsync(cb.denO, 0, M * sizeof(double), st);
         if (cb.sc_n > 0) {
             const size_t smem = (size_t)cb.sc_box * (sizeof(float2) + sizeof(float));
-            scatter_staged_kernel<<<dim3(cb.sc_n, cs.N / cb.sc_rows), kScT, smem, st>>>(cs);
+            cudaError_t e = launch_pdl_ex(scatter_staged_kernel, dim3(cb.sc_n, cs.N / cb.sc_rows), dim3(kScT),
+                                          smem, st, cs);
+            if (e != cudaSuccess) return e;
         } else {
             scatter_object_kernel<<<dim3((NN + kT - 1) / kT, cs.J), kT, 0, st>>>(
                 cs.y, cs.P, cs.pos, cs.N, cs.Mc, cb.numO, cb.denO);
         }
-        max_double_kernel<<<304, kT, 0, st>>>(cb.denO, M, cb.maxO);
+        cudaError_t e = launch_pdl(max_double_kernel, dim3(304), st, (const double*)cb.denO, M, cb.maxO);
+        if (e != cudaSuccess) return e;
     }
     {
         cudaError_t e = launch_pdl(object_normalise_kernel, dim3((unsigned)((M + kT - 1) / kT)), st, cs);
@@ -859,15 +871,18 @@ cudaError_t launch_concur(const ConcurScan& cs, int concur_mode, bool update_pro
         // the object normalisation)
         cudaMemsetAsync(cb.numP, 0, NN * sizeof(double2), st);
         cudaMemsetAsync(cb.denP, 0, NN * sizeof(double), st);
-        if (cb.probe_ppt == 2)
-            probe_partial_atomic_kernel<2><<<dim3((NN / 2 + kT - 1) / kT, cb.chunks), kT, 0, st>>>(cs);
-        else
-            probe_partial_atomic_kernel<1><<<dim3((NN + kT - 1) / kT, cb.chunks), kT, 0, st>>>(cs);
-        max_double_kernel<<<(NN + kT - 1) / kT < 304 ? (NN + kT - 1) / kT : 304, kT, 0, st>>>(
-            cb.denP, (size_t)NN, cb.maxP);
-        slice_sums_kernel<<<n_slice, kT, 0, st>>>(cs.e_part, cs.n_part, cb.e_slice);
-        probe_normalise_kernel<<<(NN + kT - 1) / kT, kT, 0, st>>>(cs, n_slice);
-        return cudaGetLastError();
+        cudaError_t e =
+            cb.probe_ppt == 2
+                ? launch_pdl(probe_partial_atomic_kernel<2>, dim3((NN / 2 + kT - 1) / kT, cb.chunks), st, cs)
+                : launch_pdl(probe_partial_atomic_kernel<1>, dim3((NN + kT - 1) / kT, cb.chunks), st, cs);
+        if (e == cudaSuccess)
+            e = launch_pdl(max_double_kernel, dim3((NN + kT - 1) / kT < 304 ? (NN + kT - 1) / kT : 304), st,
+                           (const double*)cb.denP, (size_t)NN, cb.maxP);
+        if (e == cudaSuccess)
+            e = launch_pdl(slice_sums_kernel, dim3(n_slice), st, (const double*)cs.e_part, cs.n_part,
+                           cb.e_slice);
+        if (e == cudaSuccess) e = launch_pdl(probe_normalise_kernel, dim3((NN + kT - 1) / kT), st, cs, n_slice);
+        return e;
     }
     {
         cudaError_t e = launch_probe_partial(cs, st);
