@@ -98,10 +98,16 @@ typedef struct ptycho_ctx ptycho_ctx;
 void ptycho_default_opts(ptycho_opts* opts);
 
 /* Create a context on opts->device.  opts may be NULL for the defaults.
+ * Device memory of a context comes from the device's stream-ordered memory
+ * pool of this process (allocated and freed on the context's stream); the
+ * first context on a device keeps that pool's freed memory mapped for later
+ * contexts instead of returning it to the driver at each synchronisation.
  * Errors: EINVAL (bad option), ECUDA. */
 int ptycho_create(ptycho_ctx** out, const ptycho_opts* opts);
 
-/* Release every device allocation of the context.  NULL is a no-op. */
+/* Release every device allocation of the context (back to the pool, without
+ * synchronising the device) and its stream if it created one.  NULL is a
+ * no-op. */
 void ptycho_destroy(ptycho_ctx* ctx);
 
 /* Last error message of the context ("" if none); never NULL.  With
