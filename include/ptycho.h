@@ -128,7 +128,9 @@ enum { PTYCHO_LOAD_INTENSITY_DEVICE = 1u };  /* intensity is a device pointer */
  *   M_rows, M_cols  object size, each >= N
  *   obj0       host complex float32 [M_rows][M_cols], finite (initial object)
  *   probe0     host complex float32 [N][N], finite (initial probe)
- * Synchronises the context's stream.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * Synchronises the context's stream.  A scan whose ptycho_scan_bytes exceed
+ * the device's free memory fails with ENOMEM before the intensities are read
+ * (the context then holds no scan).  Errors: EINVAL, ENOMEM, ECUDA. */
 int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_rc,
                      const float* intensity, int32_t M_rows, int32_t M_cols,
                      const float* obj0, const float* probe0, uint32_t flags);

@@ -474,6 +474,24 @@ int ptycho_load_scan(ptycho_ctx* ctx, int32_t J, int32_t N, const int32_t* pos_r
     DeviceGuard dg(ctx->opts.device);
     PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     free_scan(ctx);
+    {
+        // fail before any host work or allocation when the scan cannot fit
+        const size_t need = scan_bytes(J, N, M_rows, M_cols, ctx->opts.precision, ctx->opts.divide);
+        size_t free_b = 0, total_b = 0;
+        PT_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
+        if (need > free_b) {
+            // memory freed into the stream-ordered pool counts as used: hand it back, look again
+            cudaMemPool_t pool;
+            PT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            if (cudaDeviceGetDefaultMemPool(&pool, ctx->opts.device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+            cudaGetLastError();
+            PT_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
+            if (need > free_b)
+                return fail(ctx, PTYCHO_ENOMEM, "the scan needs " + std::to_string(need) +
+                                                    " bytes of device memory; " + std::to_string(free_b) +
+                                                    " are free");
+        }
+    }
 
     // Object tiles: CSR lists of the positions whose window overlaps each tile,
     // in ascending position order (integer work, done here), for the tile

@@ -297,3 +297,27 @@ def test_validation_errors(tiny):
             r.iterate(1, 1, 1, -1)
         r.iterate(1, 1, 1, 0)
         assert r.iteration_count == 0
+
+
+def test_scan_beyond_device_memory_is_enomem(tiny):
+    """A scan whose footprint (ptycho_scan_bytes, about 1.8 TB here) exceeds
+    the device fails with ENOMEM before its intensities are read -- the buffer
+    passed is a small stand-in that is never touched -- and the context still
+    loads and runs a scan that fits."""
+    import ctypes
+    J, N = 1 << 20, 256
+    assert native.ptycho_scan_bytes(J, N, N, N) > (1 << 40)
+    pos = np.zeros((J, 2), dtype=np.int32)
+    stand_in = np.zeros(16, dtype=np.float32)
+    obj = np.ones((N, N), dtype=np.complex64)
+    probe = np.ones((N, N), dtype=np.complex64)
+    with native.Reconstruction() as r:
+        rc = native.lib().ptycho_load_scan(r.h, J, N, pos.ctypes.data_as(ctypes.c_void_p),
+                                           stand_in.ctypes.data_as(ctypes.c_void_p), N, N,
+                                           obj.ctypes.data_as(ctypes.c_void_p),
+                                           probe.ctypes.data_as(ctypes.c_void_p), 0)
+        assert rc == native.PTYCHO_ENOMEM
+        assert "device memory" in native.ptycho_last_error(r.h)
+        r.load_scan(tiny.pos, tiny.intensity, tiny.obj0, tiny.probe0)
+        r.iterate(*native.PRESETS["DC"], 2)
+        assert np.all(np.isfinite(r.errors()))
