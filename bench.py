@@ -657,6 +657,35 @@ def measure_iterate(spec, precision: str, preset: str, steps: int, warmup: int, 
             "clocks": clocks, "e2e": e2e, "design": design, "tuning": tuning}
 
 
+def measure_sp(passes: int = 3):
+    """Sequential projections (Fig. 2): passes over the 256 positions of the
+    medium workload (256^2 patterns), one divide-kernel launch (one cluster) per
+    position in scan order, timed with CUDA events on the library's stream
+    after one untimed pass.  The steps depend on each other (each updates the
+    object and the probe the next one reads), so only one cluster works at a
+    time: this is the sequential algorithm the product-space update is
+    contrasted with, not a tuned path."""
+    import torch
+    from paper_2311_11466_gb300 import native, synth
+    scan = synth.make_scan(synth.named_spec("medium"))
+    stream = torch.cuda.Stream()
+    with native.Reconstruction(stream=stream.cuda_stream) as r:
+        r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+        r.sp_iterate(1.0, 1)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        r.sp_iterate(1.0, passes)
+        t1.record(stream)
+        t1.synchronize()
+        ms = t0.elapsed_time(t1)
+    return {"value": scan.J * passes / (ms / 1e3), "unit": UNIT, "passes": passes,
+            "ms_per_pass": ms / passes, "us_per_step": ms * 1e3 / (scan.J * passes),
+            "workload": f"medium: J={scan.J}, N={scan.N}, lambda=1, scan order",
+            "timed_launches": scan.J * passes}
+
+
 def measure_serving(requests: int, rate: float, iters: int, max_active: int = 16,
                     iters_per_round: int = 10, budget_gb: int = 180):
     """The serving workload: `requests` blind RAAR(0.9) reconstructions drawn
@@ -870,6 +899,8 @@ def main():
         del t
         torch.cuda.empty_cache()
         extras["serving"] = measure_serving(args.requests, args.rate, args.e2e_iters)
+        extras["sequential_projections"] = measure_sp()
+        extra_launches += extras["sequential_projections"]["timed_launches"]
 
     if rank == 0:
         line = {
