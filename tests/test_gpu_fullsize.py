@@ -39,6 +39,29 @@ def large_ref(large):
     return x1, prob.O, prob.P, prob.last_error
 
 
+@pytest.mark.parametrize("name", ["DC", "SF", "RRR"])
+def test_large_two_iterations_other_presets(large, name):
+    """The divide kernel's other input paths at full size, two iterations so
+    the second forms x_k from the lazy re-split: DC (no y_{k-1}, no x_{k-1}),
+    SF (a = 1: y_{k-1} but no x_{k-1}), RRR (both).  Exit waves, object, probe
+    and both Fourier errors against the FP64 oracle, 2e-5 (two iterations)."""
+    abc = native.PRESETS[name]
+    prob, x = oracle_problem(large)
+    errs = []
+    for _ in range(2):
+        x = prob.iterate(x, *abc)
+        errs.append(prob.last_error)
+    with gpu_recon(large) as r:
+        r.iterate(*abc, 2)
+        O, P = r.object_probe()
+        e = r.errors()
+        xg = r.exit_waves()
+    assert rel_l2(xg, x) <= 2e-5
+    assert rel_l2(O, prob.O) <= 2e-5
+    assert rel_l2(P, prob.P) <= 2e-5
+    np.testing.assert_allclose(e, errs, rtol=2e-5)
+
+
 @pytest.mark.parametrize("concur", ["deterministic", "atomic"])
 def test_large_raar_iteration_in_full(large, large_ref, concur):
     x1, O_ref, P_ref, e_ref = large_ref
