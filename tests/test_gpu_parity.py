@@ -321,3 +321,18 @@ def test_scan_beyond_device_memory_is_enomem(tiny):
         r.load_scan(tiny.pos, tiny.intensity, tiny.obj0, tiny.probe0)
         r.iterate(*native.PRESETS["DC"], 2)
         assert np.all(np.isfinite(r.errors()))
+
+
+def test_a_zero_is_the_identity(tiny):
+    """a = 0 makes the update the identity on the exit waves (Introduction:
+    x_{k+1} = a (...) + (1 - a) x_k): after any number of iterations with
+    a = 0 the exit waves are the initial ones, bit for bit, while the
+    concur step still runs (the object and probe move)."""
+    with gpu_recon(tiny) as r:
+        x0 = r.exit_waves()
+        O0, P0 = r.object_probe()
+        r.iterate(0.0, 1.8, 2.0, 3)
+        x3 = r.exit_waves()
+        O3, P3 = r.object_probe()
+    np.testing.assert_array_equal(x3, x0)
+    assert not np.array_equal(O3, O0) and not np.array_equal(P3, P0)
