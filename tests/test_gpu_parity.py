@@ -29,9 +29,10 @@ def tiny():
     return synth.make_scan(synth.named_spec("tiny"))
 
 
-@pytest.mark.parametrize("c", [1.0, 2.0, 0.7])
+@pytest.mark.parametrize("c", [1.0, 2.0, 0.7, 0.0])
 def test_divide_step(tiny, c):
-    # (a, b) = (1, 0) makes x_1 = y = P^c_D x_0 exactly
+    # (a, b) = (1, 0) makes x_1 = y = P^c_D x_0 exactly; c = 0 makes it the
+    # identity up to the FFT round trip
     prob, x0 = oracle_problem(tiny)
     y_ref = oabc.relax(prob.project_D, c)(x0)
     with gpu_recon(tiny) as r:
