@@ -244,6 +244,40 @@ def oracle_rate(scan, side: int, min_seconds: float, max_iters: int):
     return len(idx) * len(times) / sum(times), len(times), len(idx)
 
 
+def tiny_both(local: int, iters: int = 100):
+    """The 64-position 64 x 64 scan timed in full on both sides: 100 DC
+    iterations of the FP64 oracle on the host cores and of the library on the
+    GPU (CUDA events, after 5 warm-up iterations).  At this size the GPU is
+    bound by kernel launches, not by the kernels."""
+    import numpy as np
+    import torch
+    from oracle import ptycho as optycho
+    from paper_2311_11466_gb300 import native, synth
+    scan = synth.make_scan(synth.named_spec("tiny"))
+    prob = optycho.Problem(scan.intensity.astype(np.float64), scan.pos,
+                           scan.obj0.astype(np.complex128), scan.probe0.astype(np.complex128))
+    x = optycho.exit_waves(prob.P, prob.O, scan.pos)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        x = prob.iterate(x, 1.0, 1.0, 1.0)
+    t_cpu = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=local)
+    with native.Reconstruction(device=local, stream=stream.cuda_stream) as r:
+        r.load_scan(scan.pos, scan.intensity, scan.obj0, scan.probe0)
+        r.iterate(1.0, 1.0, 1.0, 5)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.iterate(1.0, 1.0, 1.0, iters)
+        e1.record(stream)
+        e1.synchronize()
+        t_gpu = e0.elapsed_time(e1) / 1e3
+    return {"workload": f"tiny: J={scan.J}, N={scan.N}, DC, {iters} iterations",
+            "oracle": {"value": scan.J * iters / t_cpu, "unit": UNIT, "cores": _cores()},
+            "gpu": {"value": scan.J * iters / t_gpu, "unit": UNIT, "ms_per_iteration": t_gpu * 1e3 / iters}}
+
+
 def _oracle_one_thread(scan, side: int, seconds: float):
     """The same oracle timing with one BLAS/OpenMP thread, in a child process
     (the thread count of numpy's BLAS is fixed when numpy loads)."""
@@ -843,6 +877,7 @@ def main():
             cpu["one_thread"] = {"value": one["value"], "unit": UNIT, "cores": 1,
                                  "sample": f"same sample, {one['iterations']} iterations, "
                                            f"one BLAS thread"}
+        cpu["tiny_in_full"] = tiny_both(local)
     # both divide designs at 256^2 on the same scan (the default line uses the
     # one AUTO picks; this races the two)
     variants = None
@@ -875,6 +910,8 @@ def main():
     extra_launches = 2 * KERNELS_PER_ITER * 20 if variants is not None else 0
     if concur_modes is not None:
         extra_launches += (KERNELS_PER_ITER + 2) * 20
+    if cpu and cpu.get("tiny_in_full"):
+        extra_launches += KERNELS_PER_ITER * 100
 
     # the rest of the metric (tensor-core path; serving) on a single GPU only
     extras = {}
