@@ -16,6 +16,11 @@
 // in a fixed order: chunk order, or with many chunks contiguous groups of
 // chunks added in group order).  Maxima use integer atomicMax on the bit patterns of
 // non-negative IEEE values, which is order independent.
+//
+// The atomic mode builds the same sums with atomics: the object by
+// shared-memory-staged atomics (scatter_staged_kernel), the probe by
+// register-staged FP64 atomics (the same chunked pass); the order of the
+// additions then depends on timing.
 #include <algorithm>
 #include <vector>
 
